@@ -1,0 +1,325 @@
+"""Benchmark: RAAR frame-iterations/s on one GB300 for the 2500-frame 128^2
+Fermat-spiral scan over a 1024^2 object (probe refinement every 2nd step,
+eps_a/eps_Q every step), with the fused frame kernel's HBM roofline fraction,
+an end-to-end figure through the C ABI with host buffers, and the FP64 oracle
+timed on the host cores as a reported CPU baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  Under torchrun (N > 1) every rank runs an
+independent replica of the scan (the path has no exchange step on one box),
+so scaling is weak and value = all ranks' frame-iterations / slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RAAR frame-iterations/s on 1 GB300 (FP32 vs mixed) and % of HBM roofline"
+UNIT = "frame-iterations/s"
+WORKLOAD = "fermat-2500x128-obj1024"
+PROFILE = os.path.join(ROOT, "profiles", "frame_kernel_fermat2500x128.txt")
+CSRC = os.path.join(ROOT, "paper_1602_01448_gb300", "csrc")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(CSRC, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the frame kernel from the committed ncu
+    summary, or None when the kernel sources changed since it was taken."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    mh = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    mt = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
+    if not mh or not mt or mh.group(1) != kernel_source_hash():
+        return None
+    return float(mt.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_scan():
+    import synth
+    return synth.scan_fermat()
+
+
+def oracle_sample_rate(scan, amps, n_frames: int, n_steps: int = 1):
+    """FP64 oracle RAAR steps over the first n_frames frames of the scan (full
+    object): frame-iterations per second of host time."""
+    import oracle as O
+    pos = scan.pos[:n_frames]
+    a = amps[:n_frames]
+    z = O.split(scan.psi_init, scan.probe_init, pos)
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        z = O.raar_update(z, a, scan.probe_init, pos, scan.shape, 0.75)
+        O.object_update(z, scan.probe_init, pos, scan.shape)
+    dt = time.perf_counter() - t0
+    return n_frames * n_steps / dt, dt
+
+
+def host_amplitudes(scan, seed=5):
+    """Noisy amplitudes for the oracle arms, computed with the oracle's forward
+    model (the GPU arm computes its own with the library)."""
+    import oracle as O
+    import synth
+    inten = O.forward_amplitudes(scan.obj, scan.probe, scan.pos) ** 2
+    return np.sqrt(synth.poisson_intensities(inten, scan.photons, seed))
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    scan = make_scan()
+    n = 500
+    import oracle as O
+    import synth
+    inten = O.forward_amplitudes(scan.obj, scan.probe, scan.pos[:n]) ** 2
+    a = np.sqrt(synth.poisson_intensities(inten, scan.photons, 5))
+    for _ in range(args.warmup):
+        oracle_sample_rate(scan, a, n)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_sample_rate(scan, a, n)
+        times.append(dt)
+    ms = 1000.0 * float(np.mean(times))
+    val = n / (ms / 1000.0)
+    sample = f"first {n} of 2500 frames per step, full 1024^2 object, FP64 NumPy"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_1602_01448_gb300 as S
+    import synth
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scan = make_scan()
+    K, m = scan.K, scan.m
+    plan = S.Plan(scan.pos, m, scan.shape, beta=0.75, probe_every=scan.probe_every, residual_every=1,
+                  device=dev)
+    obj = torch.as_tensor(scan.obj).to(torch.complex64).to(dev)
+    probe_true = torch.as_tensor(scan.probe).to(torch.complex64).to(dev)
+    amp = plan.forward_amplitudes(obj, probe_true)
+    inten = (amp.double() ** 2).cpu().numpy()
+    amp_h = np.sqrt(synth.poisson_intensities(inten, scan.photons, 5)).astype(np.float32)
+    amp = torch.as_tensor(amp_h).to(dev)
+    psi0 = torch.as_tensor(scan.psi_init).to(torch.complex64).to(dev)
+    w0 = torch.as_tensor(scan.probe_init).to(torch.complex64).to(dev)
+    plan.raar_init(psi0, w0)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        plan.raar_step(amp)
+    torch.cuda.synchronize()
+    S.sharp_plan_set_profiling(plan.handle, True)
+    S.sharp_plan_kernel_times(plan.handle)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.raar_step(amp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms_total = e0.elapsed_time(e1)
+    kt = S.sharp_plan_kernel_times(plan.handle)
+    S.sharp_plan_set_profiling(plan.handle, False)
+    metrics = plan.metrics.cpu().numpy().tolist()
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * K * args.steps / (ms_total / 1000.0)
+
+    # roofline of the fused frame kernel: 20 m^2 B per frame-iteration
+    frame_ms, frame_n = kt["frame"]
+    t_frame = frame_ms / max(frame_n, 1) / 1000.0
+    alg_bytes = 20.0 * m * m * K
+    achieved = alg_bytes / t_frame / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    launches = sum(n for _, n in kt.values())
+
+    # end to end through the C ABI with host buffers: per step, H2D of the
+    # measured amplitudes from pinned memory, the step, D2H of the object
+    amp_pin = torch.empty(amp.shape, dtype=amp.dtype, pin_memory=True)
+    amp_pin.copy_(amp)
+    psi_pin = torch.empty(plan.psi.shape, dtype=plan.psi.dtype, pin_memory=True)
+    amp_dev = torch.empty_like(amp)
+    e2e_steps = max(4, min(args.steps, 10))
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        amp_dev.copy_(amp_pin, non_blocking=True)
+        plan.raar_step(amp_dev)
+        psi_pin.copy_(plan.psi, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        n = K
+        import oracle as O
+        inten = O.forward_amplitudes(scan.obj, scan.probe, scan.pos[:n]) ** 2
+        a_o = np.sqrt(synth.poisson_intensities(inten, scan.photons, 5))
+        rate, dt = oracle_sample_rate(scan, a_o, n, 1)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one FP64 RAAR step + object update over all {n} frames "
+                         f"(full 1024^2 object), {dt:.1f} s, NumPy single thread"}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames": K, "frame": m, "object": list(scan.shape),
+                   "beta": 0.75, "probe_every": scan.probe_every, "residual_every": 1,
+                   "photons_per_frame": scan.photons, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (c 328 MB + a 164 MB per step)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(),
+                     "kernel": "frame_kernel<128,RAAR>", "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes, "kernel_ms": t_frame * 1000.0},
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * K / (e2e_ms / 1000.0), "unit": UNIT,
+                "h2d_bytes_per_step": int(amp.numel() * 4), "d2h_bytes_per_step": int(plan.psi.numel() * 8)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "last_metrics": {"eps_a": metrics[0], "eps_q": metrics[1]},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * sharp.h -- C ABI of the GB300 (sm_103a) RAAR ptychography hot path.
+ *
+ * The library implements one iteration of RAAR (relaxed averaged alternating
+ * reflections) over all diffraction frames of a ptychographic scan, as set out
+ * in Marchesini et al., "SHARP: a distributed, GPU-based ptychographic
+ * solver", arXiv:1602.01448, Sec. 2 (forward model, Eqs. 1-6; projections and
+ * updates, Eqs. 7-10 and the reconstruction sequence of Sec. 2.2; metrics,
+ * Eqs. 11-14).
+ *
+ * Notation (Sec. 2.1): K frames of m x m pixels, object psi of ny x nx pixels,
+ * illumination (probe) w of m x m pixels, integer frame positions x_(i).
+ *
+ * Conventions for every entry point:
+ *  - Array pointers are DEVICE pointers unless a comment says HOST.  They are
+ *    owned by the caller, row-major and contiguous.  Complex values are
+ *    float2 {re, im} (complex64).  Frames are stored frame-major: K x m x m.
+ *  - Positions are int32 pairs (row, col): the top-left object pixel of each
+ *    frame (the grid x_(i) = (r mu', r nu') of Sec. 2.1).
+ *  - Fourier amplitudes are on the unitary scale of Eq. 2: a = sqrt(I) / m
+ *    when I = |DFT|^2 of the unnormalised e^{-2 pi i} transform.  The forward
+ *    DFT is the unitary e^{-2 pi i q.r} transform.
+ *  - Work is queued on the given stream; no call synchronises it unless its
+ *    comment says so.  A plan holds scratch buffers, so calls on one plan
+ *    must not overlap on the GPU (use one stream per plan).
+ *  - Every call returns SHARP_OK or an error code; the message of the last
+ *    error of the calling thread is available from sharp_last_error().
+ *    Sizes the kernels do not implement return SHARP_ERR_UNSUPPORTED_SIZE:
+ *    there is no CPU fallback.
+ *  - Scalar results (losses, residuals, metrics) are written to DEVICE
+ *    doubles so that calls stay asynchronous.
+ */
+#ifndef SHARP_H
+#define SHARP_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SHARP_OK                   0
+#define SHARP_ERR_INVALID_ARG      1  /* null pointer, bad size, position out of range, ... */
+#define SHARP_ERR_UNSUPPORTED_SIZE 2  /* frame size without a kernel (m not in {64,128}) */
+#define SHARP_ERR_CUDA             3  /* a CUDA runtime call or launch failed */
+#define SHARP_ERR_TIMEOUT          4  /* a bounded device-side wait gave up */
+#define SHARP_ERR_STATE            5  /* call order violated (e.g. step before init) */
+
+#define SHARP_PREC_FP32            0  /* FP32 data and transforms, FP64 global sums */
+
+typedef struct sharp_plan_s* sharp_plan;
+
+/* Options of the reconstruction (Sec. 2.3 user options; Sec. 2.2 sequence). */
+typedef struct {
+    float beta;          /* RAAR relaxation beta in (0.5, 1]; 0.75 by default (Sec. 2.2) */
+    int   wrap;          /* 1: object indexed modulo its size (periodic boundary, Fig. 3) */
+    int   probe_every;   /* refine the probe (Eq. 10) on steps with iter % probe_every == 0; 0 = never */
+    int   residual_every;/* eps_Q and eps_Delta (Eqs. 12, 13) on steps with iter % residual_every == 0; 0 = never */
+    int   precision;     /* SHARP_PREC_FP32 */
+} sharp_params;
+
+/* Message of the last failed call on this thread ("" if none).  Never NULL. */
+const char* sharp_last_error(void);
+
+/* Library version string, e.g. "sharp-gb300 0.1 (sm_103a)". */
+const char* sharp_version(void);
+
+/* Fills *p with the defaults: beta 0.75, wrap 0, probe_every 0,
+ * residual_every 1, precision FP32. */
+void sharp_default_params(sharp_params* p);
+
+/*
+ * Create a plan for K frames of m x m over an ny x nx object.
+ *   pos    : DEVICE int32[K][2] (row, col) top-left corners.  Copied; the call
+ *            synchronises `stream` to read them.  Without wrap every frame must
+ *            lie inside the object (0 <= row <= ny-m, 0 <= col <= nx-m); with
+ *            wrap positions are reduced modulo (ny, nx).
+ *   params : copied; NULL means sharp_default_params().
+ * Allocates the plan's scratch (illumination sum, overlap accumulators,
+ * per-tile frame lists, reduction buffers).  The per-block lists of frames
+ * that touch each image block (Sec. 2.3) are built here once, on the host.
+ * Errors: INVALID_ARG (K < 1, ny or nx < m, bad position), UNSUPPORTED_SIZE.
+ */
+int sharp_plan_create(sharp_plan* plan, int K, int m, int ny, int nx,
+                      const int32_t* pos, const sharp_params* params,
+                      cudaStream_t stream);
+
+/* Release a plan and its scratch (synchronises the device). NULL is a no-op. */
+int sharp_plan_destroy(sharp_plan plan);
+
+/*
+ * Split operator Q (Sec. 2.1, Eqs. 5-6): frames[i](r) = probe(r) * obj(r + x_(i)).
+ *   obj    : float2[ny][nx];  probe : float2[m][m];  frames : float2[K][m][m] (output).
+ */
+int sharp_q_gather(sharp_plan plan, const float2* obj, const float2* probe,
+                   float2* frames, cudaStream_t stream);
+
+/*
+ * Data projection P_a (Eq. 7): out = F* (F z / |F z|) a, frame by frame, with
+ * phase 1 where F z = 0.  in-place (out == z) is allowed.
+ *   z, out   : float2[K][m][m];  amp : float[K][m][m] (unitary scale).
+ *   resid_sq : DEVICE double[1] or NULL; receives ||P_a z - z||^2 (overwritten).
+ */
+int sharp_fourier_project(sharp_plan plan, const float2* z, const float* amp,
+                          float2* out, double* resid_sq, cudaStream_t stream);
+
+/*
+ * Object update and overlap projection (Eqs. 8-9):
+ *   obj_out = (Q*Q)^{-1} Q* z, 0 where Q*Q <= 1e-12 max(Q*Q);
+ *   z_out   = Q obj_out = P_Q z (may be NULL).
+ * Q* z is gathered per 32x32 image tile over the frames covering that tile
+ * (no atomics, deterministic).
+ *   probe : float2[m][m];  z : float2[K][m][m];  obj_out : float2[ny][nx].
+ */
+int sharp_overlap_project(sharp_plan plan, const float2* probe, const float2* z,
+                          float2* obj_out, float2* z_out, cudaStream_t stream);
+
+/*
+ * Probe update on explicit frames (Eq. 10):
+ *   probe_out(r) = sum_i conj(obj(r+x_i)) z_i(r) / sum_i |obj(r+x_i)|^2,
+ * keeping probe_old(r) where the denominator is <= 1e-12 of its maximum.
+ *   obj : float2[ny][nx];  z : float2[K][m][m];  probe_old, probe_out : float2[m][m].
+ */
+int sharp_probe_update(sharp_plan plan, const float2* obj, const float2* z,
+                       const float2* probe_old, float2* probe_out, cudaStream_t stream);
+
+/*
+ * Start a RAAR reconstruction from z^(0) = Q psi^(0) (Sec. 2.2 sequence).
+ * The frames are kept implicitly as z = w_f . psi_y(r + x_i) + c_i, where w_f
+ * is the probe that formed them; this call sets c = 0, psi_y = psi0, psi = psi0
+ * and makes probe0 the plan's current probe (computing Q*Q).
+ *   psi0 : float2[ny][nx];  probe0 : float2[m][m]
+ *   state_c : float2[K][m][m] (output);  psi_y, psi : float2[ny][nx] (outputs).
+ */
+int sharp_raar_init(sharp_plan plan, const float2* psi0, const float2* probe0,
+                    float2* state_c, float2* psi_y, float2* psi, cudaStream_t stream);
+
+/*
+ * One RAAR step, iteration number `iter` (1-based):
+ *   z^(l) = [2b P_Q P_a + (1-2b) P_a + b (I - P_Q)] z^(l-1)       (Sec. 2.2, Luke form)
+ *   psi^(l) = Q* z^(l) / Q*Q                                        (Eq. 9)
+ *   if probe_every > 0 and iter % probe_every == 0: probe from Eq. 10.
+ * One fused frame pass (gather, FFT, magnitude projection, inverse FFT,
+ * overlap scatter-add, state update) plus one image pass.
+ *   state_c, psi_y : in/out state from sharp_raar_init or the previous step.
+ *   psi     : in: psi^(l-1) (read for eps_Q); out: psi^(l).
+ *   probe   : float2[m][m] or NULL; receives the plan's current probe.
+ *   amp     : float[K][m][m] measured amplitudes (unitary scale).
+ *   metrics : DEVICE double[4] or NULL; for the iterate z^(l-1) entering the step:
+ *             [0] eps_a (Eq. 11)  [1] eps_Q (Eq. 12, projector of the probe that
+ *             formed z^(l-1))  [2] eps_Delta = ||z^(l-1) - z^(l-2)|| / ||a|| (Eq. 13,
+ *             z^(-1) = 0)  [3] ||a||.  [1] and [2] are NaN off the residual cadence,
+ *             and [2] is NaN when step iter-1 was not run on this plan.
+ * Errors: STATE if the plan was not initialised with sharp_raar_init.
+ */
+int sharp_raar_step(sharp_plan plan, float2* state_c, float2* psi_y, float2* psi,
+                    float2* probe, const float* amp, double* metrics, int iter,
+                    cudaStream_t stream);
+
+/*
+ * Solution metric eps_0 (Eq. 14) at z = Q psi, z0 = Q psi_true:
+ *   out[0] = min_phi ||D (e^{i phi} psi - psi_true)|| / ||D psi_true||, D = Q*Q of `probe`;
+ *   out[1] = object NRMSE over pixels with D >= 0.1 max D, same phase rule.
+ *   out : DEVICE double[2].
+ */
+int sharp_solution_error(sharp_plan plan, const float2* psi, const float2* psi_true,
+                         const float2* probe, double* out, cudaStream_t stream);
+
+/*
+ * Forward model (Eq. 1): amp_out[i] = |F (probe . obj(r + x_i))| on the unitary scale.
+ */
+int sharp_forward_amplitudes(sharp_plan plan, const float2* obj, const float2* probe,
+                             float* amp_out, cudaStream_t stream);
+
+/*
+ * Amplitude loss L = sum_i || |F Q(obj, probe)_i| - amp_i ||^2 (the least-squares
+ * form of Eq. 1).  loss : DEVICE double[1] (overwritten).
+ */
+int sharp_amp_loss(sharp_plan plan, const float2* obj, const float2* probe,
+                   const float* amp, double* loss, cudaStream_t stream);
+
+/*
+ * Adjoint of sharp_amp_loss.  With r_i = z_i - P_a z_i (frame FFTs recomputed):
+ *   g_obj   = grad_scale * Q* r                   (dL/d conj(obj))
+ *   g_probe = grad_scale * sum_i conj(obj(r+x_i)) r_i   (dL/d conj(probe))
+ * Outputs are overwritten.  grad_scale = 2 gives PyTorch's convention for a
+ * real loss of complex inputs.  g_probe may be NULL.
+ */
+int sharp_amp_loss_backward(sharp_plan plan, const float2* obj, const float2* probe,
+                            const float* amp, double grad_scale, float2* g_obj,
+                            float2* g_probe, cudaStream_t stream);
+
+/*
+ * Kernel timing (tracing aid; the paper reports per-kernel time shares in the
+ * Fig. 3 caption).  When enabled, every kernel launch of the plan is bracketed
+ * by CUDA events on the launching stream, classified as
+ *   0 frame pass (fused gather/FFT/projection/scatter), 1 image pass
+ *   (normalisation), 2 probe update (Eq. 10), 3 illumination sum Q*Q,
+ *   4 other (metrics, split, overlap gather, small kernels).
+ * sharp_plan_kernel_times synchronises the recorded events and returns, per
+ * class, ms_out[c] = total milliseconds and launches_out[c] = number of
+ * launches since the last call (both arrays of 5; either may be NULL), then
+ * resets the counters.  Profiling adds an event pair per launch; leave it off
+ * for production runs.
+ */
+#define SHARP_KCLASS_COUNT 5
+int sharp_plan_set_profiling(sharp_plan plan, int enable);
+int sharp_plan_kernel_times(sharp_plan plan, double* ms_out, int* launches_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHARP_H */

@@ -1,0 +1,214 @@
+// Per-frame kernels: one thread block transforms one m x m frame in registers
+// and shared memory (fft_frame.cuh).  The RAAR variant fuses, for frame i,
+//   z_i = w_f . psi_y(r + x_i) + c_i                  (implicit iterate, split Q: Sec. 2.1)
+//   Z = F z_i;  Z' = a_i Z/|Z|;  p_i = F* Z'           (P_a, Eq. 7)
+//   A(r + x_i) += conj(w) p_i  [B(r + x_i) += conj(w) z_i]   (Q* of Eqs. 8-9)
+//   c_i <- (1 - 2b) p_i + b z_i                          (RAAR state, Sec. 2.2)
+// plus the residual partial sums of Eqs. 11-13.  With P_Q y = Q (Q*y / Q*Q)
+// the Luke-form update z+ = P_Q(2b P_a z - b z) + (1-2b) P_a z + b z becomes
+// z+ = w . psi_y + c with psi_y = (2b A - b B)/D, which the image pass forms,
+// and Q* z+ = A, so B of the next step is this step's A.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fft_frame.cuh"
+#include "sharp_common.cuh"
+
+namespace sharp {
+
+// Compiler barrier between chunks of the gather/scatter loops: keeps ptxas
+// from hoisting all 32 rows of loads at once (which overflows the 128
+// registers of a 512-thread block); the other warps of the block hide the
+// latency of each chunk.
+__device__ __forceinline__ void chunk_fence() { asm volatile("" ::: "memory"); }
+// Returns v unchanged but opaque to the optimiser, so address arithmetic that
+// depends on it stays below this point instead of being hoisted above the
+// FFT (where its registers would stay live).
+__device__ __forceinline__ int pin(int v) {
+    asm volatile("" : "+r"(v));
+    return v;
+}
+constexpr int CHUNK = 4;
+// Ordinary (coherent) load: unlike ld.global.nc it stays behind chunk_fence().
+template <class T>
+__device__ __forceinline__ T ld_plain(const T* p) { return *p; }
+
+template <int M, int MODE, int FLAGS>
+__global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a) {
+    using G = Fft3<M>;
+    constexpr int NT = G::NT;
+    constexpr int TX = G::TX;
+    constexpr int MM = M * M;
+    extern __shared__ float2 S[];             // exchange buffer, then twiddles
+    float2* tw = S + G::SMEM_ELEMS;
+    __shared__ float red[32 * 5];
+
+    const int tid = threadIdx.x;
+    G::load_twiddles(tw);
+    __syncthreads();
+    const int q = tid / M;        // pass-1 layout: rows y = q + TX k, column x
+    const int x = tid % M;
+    const float inv_m = 1.0f / M;
+
+    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+
+    for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
+        const int py = a.pos[2 * i];
+        const int px = a.pos[2 * i + 1];
+        const size_t fo = (size_t)i * MM;
+        float2 v[32];
+
+        // ------------------------------------------------ form the frame
+        if constexpr (MODE == MODE_RAAR) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const int y = q + TX * k;
+                const int o = obj_index(py, px, y, x, a.ny, a.nx, a.wrap);
+                const float2 wf = ld_plain(a.w_form + y * M + x);
+                const float2 py_ = ld_plain(a.psiy + o);
+                const float2 z = cadd(cmul(wf, py_), a.c[fo + y * M + x]);
+                v[k] = z;
+                acc[2] += cabs2(z);
+                if ((k % CHUNK) == CHUNK - 1) chunk_fence();
+                if constexpr (FLAGS & RF_METRIC) {
+                    acc[3] += cabs2(csub(cmul(wf, ld_plain(a.psi + o)), z));
+                    if (a.read_e) acc[4] += cabs2(cadd(cmul(wf, py_), a.ebuf[fo + y * M + x]));
+                }
+            }
+        } else if constexpr (MODE == MODE_PROJECT) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const int y = q + TX * k;
+                v[k] = ld_plain(a.zin + fo + y * M + x);
+                if ((k % CHUNK) == CHUNK - 1) chunk_fence();
+            }
+        } else {  // AMPS, LOSS, GRAD: z = w . obj(r + x_i)
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const int y = q + TX * k;
+                const int o = obj_index(py, px, y, x, a.ny, a.nx, a.wrap);
+                v[k] = cmul(ld_plain(a.probe + y * M + x), ld_plain(a.obj + o));
+                if ((k % CHUNK) == CHUNK - 1) chunk_fence();
+            }
+        }
+
+        G::forward(v, S, tw);
+
+        // ------------------------------------------------ Fourier domain
+        const float* ai = (MODE == MODE_AMPS) ? nullptr : a.amp + fo;
+#pragma unroll
+        for (int c = 0; c < G::C3; ++c) {
+            const int ky = G::p3_ky(c);
+#pragma unroll
+            for (int s = 0; s < G::X0; ++s) {
+                const int kx = G::p3_kx(s);
+                float2& X = v[c * G::X0 + s];
+                const float m2 = cabs2(X);
+                const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
+                const float mag = m2 * rs * inv_m;     // |F z| on the unitary scale
+                if constexpr (MODE == MODE_AMPS) {
+                    a.amp_out[fo + ky * M + kx] = mag;
+                } else {
+                    const float av = __ldg(ai + ky * M + kx);
+                    const float d = av - mag;
+                    acc[0] += d * d;
+                    if constexpr (MODE == MODE_RAAR) acc[1] += av * av;
+                    if constexpr (MODE == MODE_RAAR || MODE == MODE_PROJECT) {
+                        // Z'' = (a Z/|Z|) / m so that the raw inverse gives P_a z
+                        X = m2 > 0.f ? cscale(X, av * inv_m * rs) : make_float2(av * inv_m, 0.f);
+                    } else if constexpr (MODE == MODE_GRAD) {
+                        // (Z - a Z/|Z|) / m  ->  r = z - P_a z after the raw inverse
+                        X = m2 > 0.f ? cscale(X, (inv_m - av * rs) * inv_m) : make_float2(-av * inv_m, 0.f);
+                    }
+                }
+            }
+        }
+        if constexpr (MODE == MODE_AMPS || MODE == MODE_LOSS) continue;
+
+        G::inverse(v, S, tw);
+
+        // ------------------------------------------------ epilogue
+        if constexpr (MODE == MODE_RAAR) {
+            const float b = a.beta;
+            const float cp = 1.f - 2.f * b;
+            const int epy = pin(py), epx = pin(px), enx = pin(a.nx);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const int y = q + TX * k;
+                const int o = obj_index(epy, epx, y, x, a.ny, enx, a.wrap);
+                const float2 p = v[k];
+                const float2 wf = ld_plain(a.w_form + y * M + x);
+                const float2 wp = ld_plain(a.w_proj + y * M + x);
+                const size_t e = (size_t)pin(i) * MM + y * M + x;
+                const float2 z = cadd(cmul(wf, ld_plain(a.psiy + o)), a.c[e]);
+                red_add_f2(a.accA + o, cmulc(wp, p));
+                if constexpr (FLAGS & RF_FORM_B) red_add_f2(a.accB + o, cmulc(wp, z));
+                const float2 cn = make_float2(fmaf(cp, p.x, b * z.x), fmaf(cp, p.y, b * z.y));
+                a.c[e] = cn;
+                if (a.write_e) a.ebuf[e] = csub(cn, z);
+                if ((k % CHUNK) == CHUNK - 1) chunk_fence();
+            }
+        } else if constexpr (MODE == MODE_PROJECT) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const int y = q + TX * k;
+                a.zout[fo + y * M + x] = v[k];
+                if ((k % CHUNK) == CHUNK - 1) chunk_fence();
+            }
+        } else if constexpr (MODE == MODE_GRAD) {
+            const float gs = a.gscale;
+            const int epy = pin(py), epx = pin(px), enx = pin(a.nx);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const int y = q + TX * k;
+                const int o = obj_index(epy, epx, y, x, a.ny, enx, a.wrap);
+                const float2 r = cscale(v[k], gs);
+                red_add_f2(a.g_obj + o, cmulc(ld_plain(a.probe + y * M + x), r));
+                if (a.g_probe) red_add_f2(a.g_probe + y * M + x, cmulc(ld_plain(a.obj + o), r));
+                if ((k % CHUNK) == CHUNK - 1) chunk_fence();
+            }
+        }
+    }
+
+    block_sum<NT, 5>(acc, red);
+    if (tid == 0) {
+        if constexpr (MODE == MODE_RAAR) {
+#pragma unroll
+            for (int j = 0; j < 5; ++j) atomicAdd(a.sums + j, (double)acc[j]);
+        } else if constexpr (MODE != MODE_AMPS) {
+            atomicAdd(a.sums, (double)acc[0]);
+        }
+    }
+}
+
+template <int M, int MODE, int FLAGS>
+static cudaError_t launch_one(const FrameArgs& a, cudaStream_t s) {
+    using G = Fft3<M>;
+    const size_t smem = sizeof(float2) * (G::SMEM_ELEMS + G::TW1 + G::TW2);
+    auto kern = frame_kernel<M, MODE, FLAGS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<a.K, G::NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// All kernels of one frame size (instantiated once per translation unit).
+template <int M>
+cudaError_t launch_frames_m(int mode, int flags, const FrameArgs& a, cudaStream_t s) {
+    switch (mode) {
+        case MODE_PROJECT: return launch_one<M, MODE_PROJECT, 0>(a, s);
+        case MODE_AMPS: return launch_one<M, MODE_AMPS, 0>(a, s);
+        case MODE_LOSS: return launch_one<M, MODE_LOSS, 0>(a, s);
+        case MODE_GRAD: return launch_one<M, MODE_GRAD, 0>(a, s);
+        case MODE_RAAR:
+            switch (flags & (RF_FORM_B | RF_METRIC)) {
+                case 0: return launch_one<M, MODE_RAAR, 0>(a, s);
+                case RF_FORM_B: return launch_one<M, MODE_RAAR, RF_FORM_B>(a, s);
+                case RF_METRIC: return launch_one<M, MODE_RAAR, RF_METRIC>(a, s);
+                default: return launch_one<M, MODE_RAAR, RF_FORM_B | RF_METRIC>(a, s);
+            }
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace sharp

@@ -1,0 +1,440 @@
+// Image-side kernels: illumination sum D = Q*Q, normalisation (Q*Q)^{-1},
+// split Q, overlap Q* by per-tile gathers, probe update (Eq. 10), metric
+// finalisation (Eqs. 11-13) and the solution metric (Eq. 14).
+//
+// Q* and Q*Q are gathered per 32 x 32 image tile over the list of frames that
+// touch the tile (built once per plan), so every image pixel is written by
+// exactly one thread: no atomics, a fixed summation order, and compensated
+// (Kahan) FP32 sums.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "sharp_common.cuh"
+
+namespace sharp {
+
+namespace {
+
+constexpr int GATHER_THREADS = 256;       // 32 columns x 8 row groups
+constexpr int PROBE_CHUNK = 64;           // frames per partial sum of Eq. 10
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Offset of image coordinate g inside a frame starting at p (wrap-aware);
+// returns a value >= m when g is outside the frame.
+__device__ __forceinline__ int local_offset(int g, int p, int n, int wrap, int m) {
+    int d = g - p;
+    if (wrap && d < 0) d += n;
+    return (d < 0) ? m : d;
+}
+
+// ------------------------------------------------------------------ D = Q*Q
+__global__ void w2_kernel(const float2* __restrict__ w, float* __restrict__ w2, int mm) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mm; i += gridDim.x * blockDim.x)
+        w2[i] = cabs2(w[i]);
+}
+
+__global__ void __launch_bounds__(GATHER_THREADS)
+illum_gather_kernel(const int32_t* __restrict__ pos, const int* __restrict__ tptr,
+                    const int* __restrict__ tfr, const float* __restrict__ w2, float* __restrict__ D,
+                    unsigned* __restrict__ dmax_bits, int m, int ny, int nx, int tiles_x, int wrap) {
+    const int tile = blockIdx.x;
+    const int gx = (tile % tiles_x) * TILE + (threadIdx.x & 31);
+    const int gy0 = (tile / tiles_x) * TILE + (threadIdx.x >> 5);
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int j = tptr[tile]; j < tptr[tile + 1]; ++j) {
+        const int f = tfr[j];
+        const int py = pos[2 * f], px = pos[2 * f + 1];
+        const int lx = local_offset(gx, px, nx, wrap, m);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int ly = local_offset(gy0 + 8 * r, py, ny, wrap, m);
+            if (lx < m && ly < m) kahan_add(s[r], cc[r], __ldg(w2 + ly * m + lx));
+        }
+    }
+    float mx = 0.f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int gy = gy0 + 8 * r;
+        if (gy < ny && gx < nx) {
+            D[gy * nx + gx] = s[r];
+            mx = fmaxf(mx, s[r]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(dmax_bits, __float_as_uint(mx));
+}
+
+__global__ void invd_kernel(const float* __restrict__ D, float* __restrict__ invD,
+                            const unsigned* __restrict__ dmax_bits, int n) {
+    const float thr = 1e-12f * __uint_as_float(*dmax_bits);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float d = D[i];
+        invD[i] = d > thr ? 1.0f / d : 0.0f;
+    }
+}
+
+// ------------------------------------------------------------------ Q* z
+__global__ void __launch_bounds__(GATHER_THREADS)
+overlap_gather_kernel(const int32_t* __restrict__ pos, const int* __restrict__ tptr,
+                      const int* __restrict__ tfr, const float2* __restrict__ w,
+                      const float2* __restrict__ z, float2* __restrict__ img, int m, int ny, int nx,
+                      int tiles_x, int wrap) {
+    const int tile = blockIdx.x;
+    const int gx = (tile % tiles_x) * TILE + (threadIdx.x & 31);
+    const int gy0 = (tile / tiles_x) * TILE + (threadIdx.x >> 5);
+    float sr[4] = {0.f, 0.f, 0.f, 0.f}, si[4] = {0.f, 0.f, 0.f, 0.f};
+    float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
+    const size_t mm = (size_t)m * m;
+    for (int j = tptr[tile]; j < tptr[tile + 1]; ++j) {
+        const int f = tfr[j];
+        const int py = pos[2 * f], px = pos[2 * f + 1];
+        const int lx = local_offset(gx, px, nx, wrap, m);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int ly = local_offset(gy0 + 8 * r, py, ny, wrap, m);
+            if (lx < m && ly < m) {
+                const int l = ly * m + lx;
+                const float2 t = cmulc(__ldg(w + l), __ldg(z + f * mm + l));
+                kahan_add(sr[r], cr[r], t.x);
+                kahan_add(si[r], ci[r], t.y);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int gy = gy0 + 8 * r;
+        if (gy < ny && gx < nx) img[gy * nx + gx] = make_float2(sr[r], si[r]);
+    }
+}
+
+__global__ void scale_invd_kernel(float2* __restrict__ img, const float* __restrict__ invD, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        img[i] = cscale(img[i], invD[i]);
+}
+
+// ------------------------------------------------------------------ Q psi
+__global__ void q_gather_kernel(const int32_t* __restrict__ pos, const float2* __restrict__ obj,
+                                const float2* __restrict__ w, float2* __restrict__ frames, int K, int m,
+                                int ny, int nx, int wrap) {
+    const size_t mm = (size_t)m * m;
+    const size_t total = (size_t)K * mm;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int f = (int)(e / mm);
+        const int l = (int)(e - (size_t)f * mm);
+        const int y = l / m, x = l - y * m;
+        const int o = obj_index(pos[2 * f], pos[2 * f + 1], y, x, ny, nx, wrap);
+        frames[e] = cmul(__ldg(w + l), __ldg(obj + o));
+    }
+}
+
+// ------------------------------------------------------------------ RAAR image pass
+// psi_y = (2b A - b B) / D ; psi = A / D ; B <- 0 (it becomes the next A).
+__global__ void normalise_kernel(const float2* __restrict__ A, float2* __restrict__ B,
+                                 const float* __restrict__ invD, float2* __restrict__ psiy,
+                                 float2* __restrict__ psi, float beta, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float2 a = A[i];
+        const float2 b = B[i];
+        const float id = invD[i];
+        const float ka = 2.f * beta * id, kb = beta * id;
+        psiy[i] = make_float2(fmaf(ka, a.x, -kb * b.x), fmaf(ka, a.y, -kb * b.y));
+        psi[i] = cscale(a, id);
+        B[i] = make_float2(0.f, 0.f);
+    }
+}
+
+// ------------------------------------------------------------------ Eq. 10
+// Partial sums over a chunk of frames, one thread per probe pixel:
+//   num = sum conj(psi(r + x_i)) z_i(r),  den = sum |psi(r + x_i)|^2
+// with z_i = w . psi_y(r + x_i) + c_i (state) or z_i given (frames).
+__global__ void probe_partial_kernel(const int32_t* __restrict__ pos, const float2* __restrict__ psi,
+                                     const float2* __restrict__ zc, const float2* __restrict__ psiy,
+                                     const float2* __restrict__ w, float* __restrict__ part, int K, int m,
+                                     int ny, int nx, int wrap) {
+    const int mm = m * m;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= mm) return;
+    const int chunk = blockIdx.y;
+    const int y = l / m, x = l - y * m;
+    const int f0 = chunk * PROBE_CHUNK;
+    const int f1 = min(K, f0 + PROBE_CHUNK);
+    const float2 wl = psiy ? __ldg(w + l) : make_float2(0.f, 0.f);
+    float nr = 0.f, ni = 0.f, dn = 0.f;
+    for (int f = f0; f < f1; ++f) {
+        const int o = obj_index(pos[2 * f], pos[2 * f + 1], y, x, ny, nx, wrap);
+        const float2 ps = __ldg(psi + o);
+        float2 z = __ldg(zc + (size_t)f * mm + l);
+        if (psiy) z = cadd(z, cmul(wl, __ldg(psiy + o)));
+        const float2 t = cmulc(ps, z);
+        nr += t.x;
+        ni += t.y;
+        dn += cabs2(ps);
+    }
+    float* pc = part + (size_t)chunk * 3 * mm;
+    pc[l] = nr;
+    pc[mm + l] = ni;
+    pc[2 * mm + l] = dn;
+}
+
+__global__ void probe_reduce_kernel(const float* __restrict__ part, double* __restrict__ acc, int chunks,
+                                    int mm, unsigned long long* __restrict__ dmax) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    double nr = 0.0, ni = 0.0, dn = 0.0;
+    if (l < mm) {
+        for (int c = 0; c < chunks; ++c) {
+            const float* pc = part + (size_t)c * 3 * mm;
+            nr += pc[l];
+            ni += pc[mm + l];
+            dn += pc[2 * mm + l];
+        }
+        acc[l] = nr;
+        acc[mm + l] = ni;
+        acc[2 * mm + l] = dn;
+    }
+    // dn >= 0, so its bit pattern orders like the value
+    unsigned long long bits = (unsigned long long)__double_as_longlong(dn);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+        bits = ob > bits ? ob : bits;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(dmax, bits);
+}
+
+__global__ void probe_final_kernel(const double* __restrict__ acc, const float2* __restrict__ w_old,
+                                   float2* __restrict__ w_new, int mm,
+                                   const unsigned long long* __restrict__ dmax) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= mm) return;
+    const double thr = 1e-12 * __longlong_as_double((long long)*dmax);
+    const double dn = acc[2 * mm + l];
+    if (dn > thr) {
+        w_new[l] = make_float2((float)(acc[l] / dn), (float)(acc[mm + l] / dn));
+    } else {
+        w_new[l] = w_old[l];
+    }
+}
+
+// ------------------------------------------------------------------ metrics
+__global__ void metrics_final_kernel(const double* __restrict__ sums, double* __restrict__ out, int have_q,
+                                     int have_d, int delta_is_norm) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double a2 = sums[S_A2];
+    const double na = sqrt(a2);
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    out[0] = sqrt(sums[S_RESID]) / na;
+    out[1] = have_q ? sqrt(sums[S_Q]) / na : nan;
+    out[2] = have_d ? sqrt(delta_is_norm ? sums[S_Z2] : sums[S_D]) / na : nan;
+    out[3] = na;
+}
+
+__global__ void copy_scaled_kernel(const double* src, double* dst, double scale) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = *src * scale;
+}
+
+// ------------------------------------------------------------------ Eq. 14
+// sums: 0,1 Re/Im <u,v>, 2 |v|^2, 3,4 Re/Im <psi,psi_t>_sel, 5 |psi_t|^2_sel,
+//       6 |phi u - v|^2, 7 |phi' psi - psi_t|^2_sel ; u = D psi, v = D psi_t
+__device__ __forceinline__ void block_add_double(double (&v)[6], double* sh, double* dst) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) sh[j * 32 + warp] = v[j];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            double s = lane < nw ? sh[j * 32 + lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0 && s != 0.0) atomicAdd(dst + j, s);
+        }
+    }
+}
+
+__global__ void sol_pass1_kernel(const float2* __restrict__ psi, const float2* __restrict__ pt,
+                                 const float* __restrict__ D, const unsigned* __restrict__ dmax_bits,
+                                 double* __restrict__ sums, int n) {
+    __shared__ double sh[6 * 32];
+    const double sel_thr = 0.1 * (double)__uint_as_float(*dmax_bits);
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double d = D[i];
+        const double ur = d * psi[i].x, ui = d * psi[i].y;
+        const double vr = d * pt[i].x, vi = d * pt[i].y;
+        v[0] += ur * vr + ui * vi;
+        v[1] += ur * vi - ui * vr;
+        v[2] += vr * vr + vi * vi;
+        if (d >= sel_thr) {
+            const double ar = psi[i].x, ai = psi[i].y, br = pt[i].x, bi = pt[i].y;
+            v[3] += ar * br + ai * bi;
+            v[4] += ar * bi - ai * br;
+            v[5] += br * br + bi * bi;
+        }
+    }
+    block_add_double(v, sh, sums);
+}
+
+__global__ void sol_pass2_kernel(const float2* __restrict__ psi, const float2* __restrict__ pt,
+                                 const float* __restrict__ D, const unsigned* __restrict__ dmax_bits,
+                                 double* __restrict__ sums, int n) {
+    __shared__ double sh[6 * 32];
+    const double sel_thr = 0.1 * (double)__uint_as_float(*dmax_bits);
+    double p1r = sums[0], p1i = sums[1];
+    double a1 = sqrt(p1r * p1r + p1i * p1i);
+    if (a1 > 0) { p1r /= a1; p1i /= a1; } else { p1r = 1; p1i = 0; }
+    double p2r = sums[3], p2i = sums[4];
+    double a2 = sqrt(p2r * p2r + p2i * p2i);
+    if (a2 > 0) { p2r /= a2; p2i /= a2; } else { p2r = 1; p2i = 0; }
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double d = D[i];
+        const double ar = psi[i].x, ai = psi[i].y, br = pt[i].x, bi = pt[i].y;
+        const double er = d * (p1r * ar - p1i * ai - br), ei = d * (p1r * ai + p1i * ar - bi);
+        v[0] += er * er + ei * ei;
+        if (d >= sel_thr) {
+            const double fr = p2r * ar - p2i * ai - br, fi = p2r * ai + p2i * ar - bi;
+            v[1] += fr * fr + fi * fi;
+        }
+    }
+    block_add_double(v, sh, sums + 6);
+}
+
+__global__ void sol_final_kernel(const double* __restrict__ sums, double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        out[0] = sqrt(sums[6] / sums[2]);
+        out[1] = sqrt(sums[7] / sums[5]);
+    }
+}
+
+inline int grid_for(size_t n, int threads, int cap = 152 * 16) {
+    size_t g = (n + threads - 1) / threads;
+    if (g > (size_t)cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------- launchers
+static cudaError_t illum_for(const Plan& p, const float2* w, float* w2, float* D, unsigned* dmax,
+                             cudaStream_t s) {
+    const int mm = p.m * p.m;
+    w2_kernel<<<grid_for(mm, 256), 256, 0, s>>>(w, w2, mm);
+    cudaError_t e = cudaMemsetAsync(dmax, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    illum_gather_kernel<<<p.tiles_y * p.tiles_x, GATHER_THREADS, 0, s>>>(
+        p.pos, p.tile_ptr, p.tile_frames, w2, D, dmax, p.m, p.ny, p.nx, p.tiles_x, p.prm.wrap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_illumination(const Plan& p, const float2* w, float* w2, float* D, float* invD,
+                                unsigned* dmax_bits, cudaStream_t s) {
+    cudaError_t e = illum_for(p, w, w2, D, dmax_bits, s);
+    if (e != cudaSuccess) return e;
+    const int n = p.ny * p.nx;
+    invd_kernel<<<grid_for(n, 256), 256, 0, s>>>(D, invD, dmax_bits, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normalise(Plan& p, float2* psiy, float2* psi, cudaStream_t s) {
+    const int n = p.ny * p.nx;
+    normalise_kernel<<<grid_for(n, 256), 256, 0, s>>>(p.accA, p.accB, p.invD, psiy, psi, p.prm.beta, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_q_gather(const Plan& p, const float2* obj, const float2* probe, float2* frames,
+                            cudaStream_t s) {
+    const size_t total = (size_t)p.K * p.m * p.m;
+    q_gather_kernel<<<grid_for(total, 256, 152 * 32), 256, 0, s>>>(p.pos, obj, probe, frames, p.K, p.m, p.ny,
+                                                                   p.nx, p.prm.wrap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_overlap_gather(const Plan& p, const float2* probe, const float2* z, float2* img,
+                                  cudaStream_t s) {
+    overlap_gather_kernel<<<p.tiles_y * p.tiles_x, GATHER_THREADS, 0, s>>>(
+        p.pos, p.tile_ptr, p.tile_frames, probe, z, img, p.m, p.ny, p.nx, p.tiles_x, p.prm.wrap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_invD(const Plan& p, float2* img, const float* invD, cudaStream_t s) {
+    const int n = p.ny * p.nx;
+    scale_invd_kernel<<<grid_for(n, 256), 256, 0, s>>>(img, invD, n);
+    return cudaGetLastError();
+}
+
+static cudaError_t probe_common(Plan& p, const float2* psi, const float2* zc, const float2* psiy,
+                                const float2* wform, const float2* w_old, float2* w_out, cudaStream_t s) {
+    const int mm = p.m * p.m;
+    dim3 g((mm + 255) / 256, p.probe_chunks);
+    probe_partial_kernel<<<g, 256, 0, s>>>(p.pos, psi, zc, psiy, wform, p.probe_part, p.K, p.m, p.ny, p.nx,
+                                          p.prm.wrap);
+    unsigned long long* dmax = reinterpret_cast<unsigned long long*>(p.scal);
+    cudaError_t e = cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    probe_reduce_kernel<<<(mm + 255) / 256, 256, 0, s>>>(p.probe_part, p.probe_acc, p.probe_chunks, mm, dmax);
+    probe_final_kernel<<<(mm + 255) / 256, 256, 0, s>>>(p.probe_acc, w_old, w_out, mm, dmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe_update_state(Plan& p, const float2* c, const float2* psiy, const float2* psi,
+                                      cudaStream_t s) {
+    // z^(l) = w_cur . psi_y + c; the refined probe replaces w_cur, and the old
+    // one becomes w_form (it formed the iterate).
+    float2* old = p.w_cur;
+    p.w_cur = p.w_form;
+    p.w_form = old;
+    return probe_common(p, psi, c, psiy, p.w_form, p.w_form, p.w_cur, s);
+}
+
+cudaError_t launch_probe_update_frames(Plan& p, const float2* obj, const float2* z, const float2* w_old,
+                                       float2* w_out, cudaStream_t s) {
+    return probe_common(p, obj, z, nullptr, nullptr, w_old, w_out, s);
+}
+
+cudaError_t launch_metrics_finalize(const Plan& p, double* metrics, int have_q, int have_d, int delta_is_norm,
+                                    cudaStream_t s) {
+    metrics_final_kernel<<<1, 32, 0, s>>>(p.sums, metrics, have_q, have_d, delta_is_norm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_scaled(const double* src, double* dst, double scale, cudaStream_t s) {
+    copy_scaled_kernel<<<1, 32, 0, s>>>(src, dst, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solution_error(Plan& p, const float2* psi, const float2* psi_true, const float2* probe,
+                                  double* out, cudaStream_t s) {
+    // D of the given probe goes to the plan's scratch images (the RAAR
+    // state's own D is untouched).
+    const int n = p.ny * p.nx;
+    float* D = p.Dtmp;
+    unsigned* dmax = reinterpret_cast<unsigned*>(p.scal + 2);
+    cudaError_t e = illum_for(p, probe, p.w2tmp, D, dmax, s);
+    if (e != cudaSuccess) return e;
+    double* sums = p.scal + 4;   // 12 doubles
+    e = cudaMemsetAsync(sums, 0, 8 * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    const int g = grid_for(n, 256, 152 * 4);
+    sol_pass1_kernel<<<g, 256, 0, s>>>(psi, psi_true, D, dmax, sums, n);
+    sol_pass2_kernel<<<g, 256, 0, s>>>(psi, psi_true, D, dmax, sums, n);
+    sol_final_kernel<<<1, 32, 0, s>>>(sums, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sharp

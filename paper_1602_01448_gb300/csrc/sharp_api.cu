@@ -1,0 +1,461 @@
+// C ABI of the library (include/sharp.h): argument checks, plan scratch,
+// per-block frame lists, and the order of kernel launches of each call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sharp_common.cuh"
+
+using sharp::Plan;
+
+struct sharp_plan_s {
+    Plan p;
+};
+
+namespace {
+
+// Kernel timing: an event pair per launch, read back on demand.
+struct Prof {
+    struct Rec { int cls, kernels; cudaEvent_t a, b; };
+    std::vector<Rec> live;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+
+enum KClass { K_FRAME = 0, K_IMAGE = 1, K_PROBE = 2, K_ILLUM = 3, K_OTHER = 4 };
+
+// Bracket the launches issued by `body` with events when profiling is on.
+template <class F>
+cudaError_t timed(Plan& p, int cls, int kernels, cudaStream_t s, F body) {
+    Prof* pr = static_cast<Prof*>(p.prof);
+    if (!pr) return body();
+    cudaEvent_t a = pr->get(), b = pr->get();
+    cudaEventRecord(a, s);
+    cudaError_t e = body();
+    cudaEventRecord(b, s);
+    pr->live.push_back({cls, kernels, a, b});
+    return e;
+}
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define SHARP_CK(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) return fail(SHARP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define SHARP_NONNULL(ptr)                                                               \
+    do {                                                                                 \
+        if (!(ptr)) return fail(SHARP_ERR_INVALID_ARG, "%s: %s is NULL", __func__, #ptr); \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+bool supported_m(int m) { return m == 64 || m == 128; }
+
+void free_plan(Plan& p) {
+    void* ptrs[] = {p.pos,   p.tile_ptr,   p.tile_frames, p.w_cur, p.w_form,     p.w2,
+                    p.Dsum,  p.invD,       p.dmax_bits,   p.accA,  p.accB,       p.ebuf,
+                    p.sums,  p.probe_part, p.probe_acc,   p.scal,  p.w2tmp,      p.Dtmp,
+                    p.invDtmp};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    std::memset(&p, 0, sizeof(p));
+}
+
+sharp::FrameArgs base_args(const Plan& p) {
+    sharp::FrameArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.K = p.K;
+    a.m = p.m;
+    a.ny = p.ny;
+    a.nx = p.nx;
+    a.wrap = p.prm.wrap;
+    a.pos = p.pos;
+    a.beta = p.prm.beta;
+    a.sums = p.sums;
+    return a;
+}
+
+int check_plan(sharp_plan plan) {
+    if (!plan) return fail(SHARP_ERR_INVALID_ARG, "plan is NULL");
+    return SHARP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sharp_last_error(void) { return g_err.c_str(); }
+
+const char* sharp_version(void) { return "sharp-gb300 0.1 (sm_103a)"; }
+
+void sharp_default_params(sharp_params* p) {
+    if (!p) return;
+    p->beta = 0.75f;
+    p->wrap = 0;
+    p->probe_every = 0;
+    p->residual_every = 1;
+    p->precision = SHARP_PREC_FP32;
+}
+
+int sharp_plan_create(sharp_plan* out, int K, int m, int ny, int nx, const int32_t* pos,
+                      const sharp_params* params, cudaStream_t stream) {
+    g_err.clear();
+    SHARP_NONNULL(out);
+    *out = nullptr;
+    SHARP_NONNULL(pos);
+    if (K < 1) return fail(SHARP_ERR_INVALID_ARG, "K = %d < 1", K);
+    if (m < 1 || ny < m || nx < m) return fail(SHARP_ERR_INVALID_ARG, "need 1 <= m <= ny, nx (m=%d ny=%d nx=%d)", m, ny, nx);
+    if (!supported_m(m)) return fail(SHARP_ERR_UNSUPPORTED_SIZE, "frame size m=%d has no kernel (64, 128)", m);
+    if ((long long)ny * nx > (1LL << 30) || (long long)K * m * m > (1LL << 34))
+        return fail(SHARP_ERR_INVALID_ARG, "problem too large for 32-bit pixel indexing");
+    sharp_params prm;
+    sharp_default_params(&prm);
+    if (params) prm = *params;
+    if (!(prm.beta > 0.f && prm.beta <= 1.f)) return fail(SHARP_ERR_INVALID_ARG, "beta = %g outside (0, 1]", prm.beta);
+    if (prm.probe_every < 0 || prm.residual_every < 0) return fail(SHARP_ERR_INVALID_ARG, "negative cadence");
+    if (prm.precision != SHARP_PREC_FP32) return fail(SHARP_ERR_INVALID_ARG, "unknown precision %d", prm.precision);
+
+    std::vector<int32_t> hpos((size_t)K * 2);
+    SHARP_CK(cudaMemcpyAsync(hpos.data(), pos, hpos.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    SHARP_CK(cudaStreamSynchronize(stream));
+    for (int i = 0; i < K; ++i) {
+        int r = hpos[2 * i], c = hpos[2 * i + 1];
+        if (prm.wrap) {
+            r %= ny; if (r < 0) r += ny;
+            c %= nx; if (c < 0) c += nx;
+            hpos[2 * i] = r;
+            hpos[2 * i + 1] = c;
+        } else if (r < 0 || c < 0 || r > ny - m || c > nx - m) {
+            return fail(SHARP_ERR_INVALID_ARG, "frame %d at (%d, %d) leaves the %dx%d object (no wrap)", i, r, c, ny, nx);
+        }
+    }
+    // per-tile frame lists: the tiles each frame touches (wrap-aware)
+    const int tiles_y = (ny + sharp::TILE - 1) / sharp::TILE;
+    const int tiles_x = (nx + sharp::TILE - 1) / sharp::TILE;
+    std::vector<std::vector<int>> rows_of(K), cols_of(K);
+    std::vector<int> count((size_t)tiles_y * tiles_x + 1, 0);
+    std::vector<char> mark_y(tiles_y), mark_x(tiles_x);
+    for (int i = 0; i < K; ++i) {
+        std::fill(mark_y.begin(), mark_y.end(), 0);
+        std::fill(mark_x.begin(), mark_x.end(), 0);
+        for (int d = 0; d < m; ++d) {
+            mark_y[((hpos[2 * i] + d) % ny) / sharp::TILE] = 1;
+            mark_x[((hpos[2 * i + 1] + d) % nx) / sharp::TILE] = 1;
+        }
+        for (int t = 0; t < tiles_y; ++t) if (mark_y[t]) rows_of[i].push_back(t);
+        for (int t = 0; t < tiles_x; ++t) if (mark_x[t]) cols_of[i].push_back(t);
+        for (int ty : rows_of[i]) for (int tx : cols_of[i]) count[(size_t)ty * tiles_x + tx + 1]++;
+    }
+    for (size_t t = 1; t < count.size(); ++t) count[t] += count[t - 1];
+    const int nnz = count.back();
+    std::vector<int> frames(nnz), fill(count.begin(), count.end() - 1);
+    for (int i = 0; i < K; ++i)
+        for (int ty : rows_of[i]) for (int tx : cols_of[i]) frames[fill[(size_t)ty * tiles_x + tx]++] = i;
+
+    sharp_plan h = new sharp_plan_s;
+    Plan& p = h->p;
+    std::memset(&p, 0, sizeof(p));
+    p.K = K; p.m = m; p.ny = ny; p.nx = nx; p.prm = prm;
+    p.tiles_y = tiles_y; p.tiles_x = tiles_x; p.tile_nnz = nnz;
+    p.probe_chunks = (K + 63) / 64;
+    const size_t n = (size_t)ny * nx, mm = (size_t)m * m;
+    cudaError_t e = cudaSuccess;
+#define SHARP_ALLOC(field, count)                   \
+    if (e == cudaSuccess) e = dalloc(&p.field, (count));
+    SHARP_ALLOC(pos, (size_t)K * 2)
+    SHARP_ALLOC(tile_ptr, count.size())
+    SHARP_ALLOC(tile_frames, (size_t)std::max(nnz, 1))
+    SHARP_ALLOC(w_cur, mm)
+    SHARP_ALLOC(w_form, mm)
+    SHARP_ALLOC(w2, mm)
+    SHARP_ALLOC(Dsum, n)
+    SHARP_ALLOC(invD, n)
+    SHARP_ALLOC(dmax_bits, 4)
+    SHARP_ALLOC(accA, n)
+    SHARP_ALLOC(accB, n)
+    SHARP_ALLOC(sums, 16)
+    SHARP_ALLOC(probe_part, (size_t)p.probe_chunks * 3 * mm)
+    SHARP_ALLOC(probe_acc, 3 * mm)
+    SHARP_ALLOC(scal, 32)
+    SHARP_ALLOC(w2tmp, mm)
+    SHARP_ALLOC(Dtmp, n)
+    SHARP_ALLOC(invDtmp, n)
+#undef SHARP_ALLOC
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p.pos, hpos.data(), hpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p.tile_ptr, count.data(), count.size() * sizeof(int), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(p.tile_frames, frames.data(), (size_t)nnz * sizeof(int), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.scal, 0, 32 * sizeof(double), stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // host vectors die here
+    if (e != cudaSuccess) {
+        free_plan(p);
+        delete h;
+        return fail(SHARP_ERR_CUDA, "plan allocation: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return SHARP_OK;
+}
+
+int sharp_plan_set_profiling(sharp_plan plan, int enable) {
+    if (int r = check_plan(plan)) return r;
+    Plan& p = plan->p;
+    if (enable && !p.prof) p.prof = new Prof();
+    if (!enable && p.prof) {
+        Prof* pr = static_cast<Prof*>(p.prof);
+        cudaDeviceSynchronize();
+        for (auto& r : pr->live) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        for (auto e : pr->pool) cudaEventDestroy(e);
+        delete pr;
+        p.prof = nullptr;
+    }
+    return SHARP_OK;
+}
+
+int sharp_plan_kernel_times(sharp_plan plan, double* ms_out, int* launches_out) {
+    if (int r = check_plan(plan)) return r;
+    double ms[SHARP_KCLASS_COUNT] = {0, 0, 0, 0, 0};
+    int cnt[SHARP_KCLASS_COUNT] = {0, 0, 0, 0, 0};
+    Prof* pr = static_cast<Prof*>(plan->p.prof);
+    if (pr) {
+        for (auto& r : pr->live) {
+            SHARP_CK(cudaEventSynchronize(r.b));
+            float t = 0.f;
+            SHARP_CK(cudaEventElapsedTime(&t, r.a, r.b));
+            ms[r.cls] += t;
+            cnt[r.cls] += r.kernels;
+            pr->pool.push_back(r.a);
+            pr->pool.push_back(r.b);
+        }
+        pr->live.clear();
+    }
+    for (int c = 0; c < SHARP_KCLASS_COUNT; ++c) {
+        if (ms_out) ms_out[c] = ms[c];
+        if (launches_out) launches_out[c] = cnt[c];
+    }
+    return SHARP_OK;
+}
+
+int sharp_plan_destroy(sharp_plan plan) {
+    if (!plan) return SHARP_OK;
+    cudaDeviceSynchronize();
+    sharp_plan_set_profiling(plan, 0);
+    free_plan(plan->p);
+    delete plan;
+    return SHARP_OK;
+}
+
+int sharp_q_gather(sharp_plan plan, const float2* obj, const float2* probe, float2* frames, cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    SHARP_NONNULL(obj); SHARP_NONNULL(probe); SHARP_NONNULL(frames);
+    SHARP_CK(sharp::launch_q_gather(plan->p, obj, probe, frames, s));
+    return SHARP_OK;
+}
+
+int sharp_fourier_project(sharp_plan plan, const float2* z, const float* amp, float2* out, double* resid_sq,
+                          cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    SHARP_NONNULL(z); SHARP_NONNULL(amp); SHARP_NONNULL(out);
+    Plan& p = plan->p;
+    SHARP_CK(cudaMemsetAsync(p.sums, 0, sizeof(double), s));
+    sharp::FrameArgs a = base_args(p);
+    a.zin = z;
+    a.zout = out;
+    a.amp = amp;
+    SHARP_CK(sharp::launch_frames(sharp::MODE_PROJECT, 0, a, s));
+    if (resid_sq) SHARP_CK(sharp::launch_copy_scaled(p.sums, resid_sq, 1.0, s));
+    return SHARP_OK;
+}
+
+int sharp_overlap_project(sharp_plan plan, const float2* probe, const float2* z, float2* obj_out, float2* z_out,
+                          cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    SHARP_NONNULL(probe); SHARP_NONNULL(z); SHARP_NONNULL(obj_out);
+    Plan& p = plan->p;
+    unsigned* dmax = reinterpret_cast<unsigned*>(p.scal + 3);
+    SHARP_CK(sharp::launch_illumination(p, probe, p.w2tmp, p.Dtmp, p.invDtmp, dmax, s));
+    SHARP_CK(sharp::launch_overlap_gather(p, probe, z, obj_out, s));
+    SHARP_CK(sharp::launch_scale_invD(p, obj_out, p.invDtmp, s));
+    if (z_out) SHARP_CK(sharp::launch_q_gather(p, obj_out, probe, z_out, s));
+    return SHARP_OK;
+}
+
+int sharp_probe_update(sharp_plan plan, const float2* obj, const float2* z, const float2* probe_old,
+                       float2* probe_out, cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    SHARP_NONNULL(obj); SHARP_NONNULL(z); SHARP_NONNULL(probe_old); SHARP_NONNULL(probe_out);
+    if (probe_out == probe_old) return fail(SHARP_ERR_INVALID_ARG, "probe_out must not alias probe_old");
+    SHARP_CK(sharp::launch_probe_update_frames(plan->p, obj, z, probe_old, probe_out, s));
+    return SHARP_OK;
+}
+
+int sharp_raar_init(sharp_plan plan, const float2* psi0, const float2* probe0, float2* state_c, float2* psi_y,
+                    float2* psi, cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    SHARP_NONNULL(psi0); SHARP_NONNULL(probe0); SHARP_NONNULL(state_c); SHARP_NONNULL(psi_y); SHARP_NONNULL(psi);
+    Plan& p = plan->p;
+    const size_t n = (size_t)p.ny * p.nx, mm = (size_t)p.m * p.m;
+    SHARP_CK(cudaMemcpyAsync(p.w_cur, probe0, mm * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    SHARP_CK(cudaMemcpyAsync(p.w_form, probe0, mm * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    SHARP_CK(sharp::launch_illumination(p, p.w_cur, p.w2, p.Dsum, p.invD, p.dmax_bits, s));
+    SHARP_CK(cudaMemsetAsync(state_c, 0, (size_t)p.K * mm * sizeof(float2), s));
+    if (psi_y != psi0) SHARP_CK(cudaMemcpyAsync(psi_y, psi0, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    if (psi != psi0) SHARP_CK(cudaMemcpyAsync(psi, psi0, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    SHARP_CK(cudaMemsetAsync(p.accA, 0, n * sizeof(float2), s));
+    SHARP_CK(cudaMemsetAsync(p.accB, 0, n * sizeof(float2), s));
+    p.b_valid = false;
+    p.form_differs = false;
+    p.e_written_iter = 0;
+    p.last_iter = 0;
+    p.initialised = true;
+    return SHARP_OK;
+}
+
+int sharp_raar_step(sharp_plan plan, float2* state_c, float2* psi_y, float2* psi, float2* probe, const float* amp,
+                    double* metrics, int iter, cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    SHARP_NONNULL(state_c); SHARP_NONNULL(psi_y); SHARP_NONNULL(psi); SHARP_NONNULL(amp);
+    Plan& p = plan->p;
+    if (!p.initialised) return fail(SHARP_ERR_STATE, "sharp_raar_step before sharp_raar_init");
+    if (iter < 1) return fail(SHARP_ERR_INVALID_ARG, "iter = %d < 1", iter);
+    const size_t mm = (size_t)p.m * p.m;
+    const int R = p.prm.residual_every;
+    const bool cadence = R > 0 && iter % R == 0;
+    const bool write_e = R > 0 && (iter + 1) % R == 0;
+    int flags = 0;
+    if (!p.b_valid) flags |= sharp::RF_FORM_B;
+    int have_q = 0, have_d = 0, delta_is_norm = 0, read_e = 0;
+    if (cadence) {
+        flags |= sharp::RF_METRIC;
+        have_q = 1;
+        if (p.last_iter == 0) {
+            have_d = 1;
+            delta_is_norm = 1;   // z^(-1) = 0
+        } else if (p.e_written_iter == iter - 1 && p.last_iter == iter - 1) {
+            have_d = 1;
+            read_e = 1;
+        }
+    }
+    if ((read_e || write_e) && !p.ebuf) {
+        SHARP_CK(dalloc(&p.ebuf, (size_t)p.K * mm));
+    }
+    SHARP_CK(cudaMemsetAsync(p.sums, 0, 8 * sizeof(double), s));
+    sharp::FrameArgs a = base_args(p);
+    a.c = state_c;
+    a.psiy = psi_y;
+    a.psi = psi;
+    a.ebuf = p.ebuf;
+    a.w_form = p.w_form;
+    a.w_proj = p.w_cur;
+    a.accA = p.accA;
+    a.accB = p.accB;
+    a.amp = amp;
+    a.read_e = read_e;
+    a.write_e = write_e ? 1 : 0;
+    SHARP_CK(timed(p, K_FRAME, 1, s, [&] { return sharp::launch_frames(sharp::MODE_RAAR, flags, a, s); }));
+    SHARP_CK(timed(p, K_IMAGE, 1, s, [&] { return sharp::launch_normalise(p, psi_y, psi, s); }));
+    std::swap(p.accA, p.accB);   // B of the next step = this step's A (= Q* z^(l))
+    p.b_valid = true;
+    if (p.form_differs) {
+        SHARP_CK(cudaMemcpyAsync(p.w_form, p.w_cur, mm * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+        p.form_differs = false;
+    }
+    if (metrics)
+        SHARP_CK(timed(p, K_OTHER, 1, s, [&] {
+            return sharp::launch_metrics_finalize(p, metrics, have_q, have_d, delta_is_norm, s);
+        }));
+    if (p.prm.probe_every > 0 && iter % p.prm.probe_every == 0) {
+        SHARP_CK(timed(p, K_PROBE, 3, s, [&] { return sharp::launch_probe_update_state(p, state_c, psi_y, psi, s); }));
+        SHARP_CK(timed(p, K_ILLUM, 3, s, [&] {
+            return sharp::launch_illumination(p, p.w_cur, p.w2, p.Dsum, p.invD, p.dmax_bits, s);
+        }));
+        p.b_valid = false;
+        p.form_differs = true;
+    }
+    if (probe) SHARP_CK(cudaMemcpyAsync(probe, p.w_cur, mm * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    p.e_written_iter = write_e ? iter : 0;
+    p.last_iter = iter;
+    return SHARP_OK;
+}
+
+int sharp_solution_error(sharp_plan plan, const float2* psi, const float2* psi_true, const float2* probe,
+                         double* out, cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    SHARP_NONNULL(psi); SHARP_NONNULL(psi_true); SHARP_NONNULL(probe); SHARP_NONNULL(out);
+    SHARP_CK(sharp::launch_solution_error(plan->p, psi, psi_true, probe, out, s));
+    return SHARP_OK;
+}
+
+int sharp_forward_amplitudes(sharp_plan plan, const float2* obj, const float2* probe, float* amp_out,
+                             cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    SHARP_NONNULL(obj); SHARP_NONNULL(probe); SHARP_NONNULL(amp_out);
+    sharp::FrameArgs a = base_args(plan->p);
+    a.obj = obj;
+    a.probe = probe;
+    a.amp_out = amp_out;
+    SHARP_CK(sharp::launch_frames(sharp::MODE_AMPS, 0, a, s));
+    return SHARP_OK;
+}
+
+int sharp_amp_loss(sharp_plan plan, const float2* obj, const float2* probe, const float* amp, double* loss,
+                   cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    SHARP_NONNULL(obj); SHARP_NONNULL(probe); SHARP_NONNULL(amp); SHARP_NONNULL(loss);
+    Plan& p = plan->p;
+    SHARP_CK(cudaMemsetAsync(p.sums, 0, sizeof(double), s));
+    sharp::FrameArgs a = base_args(p);
+    a.obj = obj;
+    a.probe = probe;
+    a.amp = amp;
+    SHARP_CK(sharp::launch_frames(sharp::MODE_LOSS, 0, a, s));
+    SHARP_CK(sharp::launch_copy_scaled(p.sums, loss, 1.0, s));
+    return SHARP_OK;
+}
+
+int sharp_amp_loss_backward(sharp_plan plan, const float2* obj, const float2* probe, const float* amp,
+                            double grad_scale, float2* g_obj, float2* g_probe, cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    SHARP_NONNULL(obj); SHARP_NONNULL(probe); SHARP_NONNULL(amp); SHARP_NONNULL(g_obj);
+    Plan& p = plan->p;
+    SHARP_CK(cudaMemsetAsync(g_obj, 0, (size_t)p.ny * p.nx * sizeof(float2), s));
+    if (g_probe) SHARP_CK(cudaMemsetAsync(g_probe, 0, (size_t)p.m * p.m * sizeof(float2), s));
+    SHARP_CK(cudaMemsetAsync(p.sums, 0, sizeof(double), s));
+    sharp::FrameArgs a = base_args(p);
+    a.obj = obj;
+    a.probe = probe;
+    a.amp = amp;
+    a.g_obj = g_obj;
+    a.g_probe = g_probe;
+    a.gscale = (float)grad_scale;
+    SHARP_CK(sharp::launch_frames(sharp::MODE_GRAD, 0, a, s));
+    return SHARP_OK;
+}
+
+}  // extern "C"

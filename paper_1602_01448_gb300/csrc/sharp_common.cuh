@@ -1,0 +1,188 @@
+// Shared device helpers and the internal (C++) interface between the
+// translation units of the library.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sharp.h"
+
+namespace sharp {
+
+// ---------------------------------------------------------------- complex
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// a * b
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+// Vector reductions into global memory (sm_90+): one red.global per pixel.
+__device__ __forceinline__ void red_add_f2(float2* p, float2 v) {
+    atomicAdd(p, v);
+}
+
+// Object pixel index of frame-local (y, x) for a frame at (py, px).  With wrap
+// the positions are pre-reduced to [0, n) and m <= n, so one subtraction is
+// enough.
+__device__ __forceinline__ int obj_index(int py, int px, int y, int x, int ny, int nx, int wrap) {
+    int r = py + y, c = px + x;
+    if (wrap) {
+        r = (r >= ny) ? r - ny : r;
+        c = (c >= nx) ? c - nx : c;
+    }
+    return r * nx + c;
+}
+
+// Block-wide sum of NV floats per thread; result valid in thread 0.  `red`
+// must hold 32 * NV floats of shared memory.
+template <int NT, int NV>
+__device__ __forceinline__ void block_sum(float (&v)[NV], float* red) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NT / 32;
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) red[j * 32 + warp] = v[j];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            float s = (lane < NW) ? red[j * 32 + lane] : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            v[j] = s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- plan
+// Device-resident scratch owned by a plan.  All pointers are device pointers.
+struct Plan {
+    int K, m, ny, nx;
+    sharp_params prm;
+    int32_t* pos;            // K x 2, normalised (wrap) positions
+    // per-tile frame lists (CSR over TILE x TILE image tiles)
+    int tiles_y, tiles_x;
+    int* tile_ptr;           // tiles + 1
+    int* tile_frames;        // nnz
+    int tile_nnz;
+    // illumination
+    float2* w_cur;           // probe used by the next projection
+    float2* w_form;          // probe that formed the current iterate
+    float* w2;               // |w_cur|^2 (m*m)
+    float* Dsum;             // Q*Q (ny*nx), FP32 compensated sum
+    float* invD;             // 1/D or 0 below the threshold
+    unsigned* dmax_bits;     // max D as float bits
+    // overlap accumulators (float2 images); A = Q* P_a z, B = Q* z
+    float2* accA;
+    float2* accB;
+    bool b_valid;            // B == Q* z of the entering iterate
+    bool initialised;
+    // eps_Delta support: e = c^(l) - z^(l-1)
+    float2* ebuf;            // K*m*m or nullptr
+    int e_written_iter;      // step that last wrote ebuf (0 = none)
+    int last_iter;           // last step run (0 = none)
+    // reductions
+    double* sums;            // 16 doubles of per-step sums
+    float* probe_part;       // partial sums of the probe update (chunks x 3 x m*m)
+    int probe_chunks;
+    double* probe_acc;       // 3 x m*m doubles
+    double* scal;            // 32 doubles of misc scalars
+    // scratch for operations on a caller-given probe (standalone operators)
+    float* w2tmp;            // m*m
+    float* Dtmp;             // ny*nx
+    float* invDtmp;          // ny*nx
+    bool form_differs;       // w_form != w_cur (a probe update happened)
+    void* prof;              // kernel-timing state (sharp_api.cu), nullptr when off
+};
+
+constexpr int TILE = 32;
+
+// ------------------------------------------------ launchers (frame_kernels.cu)
+enum FrameMode { MODE_RAAR = 0, MODE_PROJECT = 1, MODE_AMPS = 2, MODE_LOSS = 3, MODE_GRAD = 4 };
+
+struct FrameArgs {
+    int K, m, ny, nx, wrap;
+    const int32_t* pos;
+    // RAAR state
+    float2* c;               // K*m*m state (in/out)
+    const float2* psiy;      // image
+    const float2* psi;       // image (eps_Q gather)
+    float2* ebuf;            // eps_Delta buffer
+    const float2* w_form;
+    const float2* w_proj;
+    float2* accA;
+    float2* accB;
+    float beta;
+    int read_e;              // accumulate |w_f psi_y + e|^2 (needs RF_METRIC)
+    int write_e;             // store e = c_new - z
+    // explicit-frame modes
+    const float2* zin;
+    float2* zout;
+    const float* amp;
+    float* amp_out;
+    const float2* obj;
+    const float2* probe;
+    float2* g_obj;
+    float2* g_probe;
+    float gscale;
+    double* sums;            // per-mode accumulators
+};
+
+// compile-time flags of MODE_RAAR
+enum RaarFlags { RF_FORM_B = 1, RF_METRIC = 2 };
+
+template <int M>
+cudaError_t launch_frames_m(int mode, int flags, const FrameArgs& a, cudaStream_t s);
+
+inline cudaError_t launch_frames(int mode, int flags, const FrameArgs& a, cudaStream_t s) {
+    if (a.K <= 0) return cudaSuccess;
+    switch (a.m) {
+        case 64: return launch_frames_m<64>(mode, flags, a, s);
+        case 128: return launch_frames_m<128>(mode, flags, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------ launchers (image_kernels.cu)
+cudaError_t launch_illumination(const Plan& p, const float2* w, float* w2, float* D, float* invD,
+                                unsigned* dmax_bits, cudaStream_t s);   // D = Q*Q of w, invD
+cudaError_t launch_normalise(Plan& p, float2* psiy, float2* psi, cudaStream_t s);
+cudaError_t launch_q_gather(const Plan& p, const float2* obj, const float2* probe, float2* frames,
+                            cudaStream_t s);
+cudaError_t launch_overlap_gather(const Plan& p, const float2* probe, const float2* z, float2* img,
+                                  cudaStream_t s);   // Q* z
+cudaError_t launch_scale_invD(const Plan& p, float2* img, const float* invD, cudaStream_t s);  // img *= invD
+cudaError_t launch_probe_update_state(Plan& p, const float2* c, const float2* psiy, const float2* psi,
+                                      cudaStream_t s);  // Eq. 10 on z = w_cur psiy + c -> w_cur
+cudaError_t launch_probe_update_frames(Plan& p, const float2* obj, const float2* z,
+                                       const float2* w_old, float2* w_out, cudaStream_t s);
+cudaError_t launch_metrics_finalize(const Plan& p, double* metrics, int have_q, int have_d,
+                                    int delta_is_norm, cudaStream_t s);
+cudaError_t launch_solution_error(Plan& p, const float2* psi, const float2* psi_true, const float2* probe,
+                                  double* out, cudaStream_t s);
+cudaError_t launch_copy_scaled(const double* src, double* dst, double scale, cudaStream_t s);
+
+// slots of Plan::sums
+enum SumSlot {
+    S_RESID = 0,   // sum (a - |Fz|)^2  = ||P_a z - z||^2
+    S_A2 = 1,      // sum a^2
+    S_Z2 = 2,      // sum |z|^2
+    S_Q = 3,       // sum |w_f psi - z|^2
+    S_D = 4,       // sum |w_f psi_y + e|^2
+};
+
+}  // namespace sharp
