@@ -280,6 +280,7 @@ def raar_reconstruct(a, pos, shape, w0, psi0, n_iter, beta=0.75, probe_every=0,
     a = np.asarray(a, dtype=np.float64)
     w = np.asarray(w0, dtype=np.complex128).copy()
     z = split(psi0, w, pos, wrap)
+    w_formed = w          # probe that formed the current iterate z
     z_prev = np.zeros_like(z)
     history = []
     psi = np.asarray(psi0, dtype=np.complex128).copy()
@@ -287,9 +288,10 @@ def raar_reconstruct(a, pos, shape, w0, psi0, n_iter, beta=0.75, probe_every=0,
         rec = {"step": step}
         if record_metrics:
             rec["eps_a"] = eps_a(z, a)
-            rec["eps_q"] = eps_q(z, a, w, pos, shape, wrap)
+            rec["eps_q"] = eps_q(z, a, w_formed, pos, shape, wrap)
             rec["eps_delta"] = eps_delta(z, z_prev, a)
         z_next = raar_update(z, a, w, pos, shape, beta, wrap, form)
+        w_formed = w
         psi = object_update(z_next, w, pos, shape, wrap)
         if probe_every and step % probe_every == 0:
             w = probe_update(z_next, psi, pos, w, wrap)

@@ -200,21 +200,21 @@ def test_reconstruct_loop_order_and_metric_convention():
     out = O.raar_reconstruct(a, s.pos, s.shape, w0, psi0, 4, beta=0.8, probe_every=2)
     w = w0.copy()
     z = O.split(psi0, w, s.pos)
-    zs, ws = [z], [w]
+    zs, formed = [z], [w]          # formed[l]: probe that formed zs[l]
     for step in range(1, 5):
         z = O.raar_update(z, a, w, s.pos, s.shape, 0.8)
+        formed.append(w)
         psi = O.object_update(z, w, s.pos, s.shape)
         if step % 2 == 0:
             w = O.probe_update(z, psi, s.pos, w)
         zs.append(z)
-        ws.append(w)
     np.testing.assert_allclose(out["z"], zs[-1], atol=1e-12)
-    np.testing.assert_allclose(out["w"], ws[-1], atol=1e-12)
+    np.testing.assert_allclose(out["w"], w, atol=1e-12)
     np.testing.assert_allclose(out["psi"], psi, atol=1e-12)
     for step, rec in enumerate(out["history"], start=1):
         zin = zs[step - 1]
         assert abs(rec["eps_a"] - O.eps_a(zin, a)) < 1e-13
-        assert abs(rec["eps_q"] - O.eps_q(zin, a, ws[step - 1], s.pos, s.shape)) < 1e-13
+        assert abs(rec["eps_q"] - O.eps_q(zin, a, formed[step - 1], s.pos, s.shape)) < 1e-13
         zprev = zs[step - 2] if step >= 2 else np.zeros_like(zin)
         assert abs(rec["eps_delta"] - O.eps_delta(zin, zprev, a)) < 1e-13
 
