@@ -118,9 +118,9 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def make_scan():
+def make_scan(frames: int = 2500):
     import synth
-    return synth.scan_fermat()
+    return synth.scan_fermat(count=frames)
 
 
 def oracle_sample_rate(scan, amps, n_frames: int, n_steps: int = 1):
@@ -183,7 +183,7 @@ def run_ours(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    scan = make_scan()
+    scan = make_scan(args.frames)
     K, m = scan.K, scan.m
     plan = S.Plan(scan.pos, m, scan.shape, beta=0.75, probe_every=scan.probe_every, residual_every=1,
                   device=dev)
@@ -279,7 +279,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frames": K, "frame": m, "object": list(scan.shape),
+        "config": {"workload": WORKLOAD if K == 2500 else f"fermat-{K}x128-obj1024", "frames": K, "frame": m, "object": list(scan.shape),
                    "beta": 0.75, "probe_every": scan.probe_every, "residual_every": 1,
                    "photons_per_frame": scan.photons, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (c 328 MB + a 164 MB per step)"},
@@ -305,6 +305,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames", type=int, default=2500,
+                    help="frames of the Fermat scan (2500 = the benchmark; fewer for small ncu captures)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

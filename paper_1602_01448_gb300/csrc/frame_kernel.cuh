@@ -2,12 +2,16 @@
 // and shared memory (fft_frame.cuh).  The RAAR variant fuses, for frame i,
 //   z_i = w_f . psi_y(r + x_i) + c_i                  (implicit iterate, split Q: Sec. 2.1)
 //   Z = F z_i;  Z' = a_i Z/|Z|;  p_i = F* Z'           (P_a, Eq. 7)
-//   A(r + x_i) += conj(w) p_i  [B(r + x_i) += conj(w) z_i]   (Q* of Eqs. 8-9)
+//   R_A(r + x_i) += conj(w) (p_i - w rho)  [R_B += conj(w) (z_i - w rho)]   (Q*, Eqs. 8-9)
 //   c_i <- (1 - 2b) p_i + b z_i                          (RAAR state, Sec. 2.2)
 // plus the residual partial sums of Eqs. 11-13.  With P_Q y = Q (Q*y / Q*Q)
 // the Luke-form update z+ = P_Q(2b P_a z - b z) + (1-2b) P_a z + b z becomes
-// z+ = w . psi_y + c with psi_y = (2b A - b B)/D, which the image pass forms,
-// and Q* z+ = A, so B of the next step is this step's A.
+// z+ = w . psi_y + c with psi_y = (2b A - b B)/D, which the image pass forms
+// from A = Q* P_a z and B = Q* z; and Q* z+ = A, so B/D of the next step is
+// this step's object A/D.  The overlap sums are accumulated relative to the
+// reference image rho = psi_y / b (A = D rho + R_A), which tends to the object
+// itself: near convergence the FP32 sums then hold only small corrections and
+// their rounding no longer sets the error floor of the object.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -131,6 +135,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a
         if constexpr (MODE == MODE_RAAR) {
             const float b = a.beta;
             const float cp = 1.f - 2.f * b;
+            const float ib = 1.f / b;
             const int epy = pin(py), epx = pin(px), enx = pin(a.nx);
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
@@ -140,9 +145,11 @@ __global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a
                 const float2 wf = ld_plain(a.w_form + y * M + x);
                 const float2 wp = ld_plain(a.w_proj + y * M + x);
                 const size_t e = (size_t)pin(i) * MM + y * M + x;
-                const float2 z = cadd(cmul(wf, ld_plain(a.psiy + o)), a.c[e]);
-                red_add_f2(a.accA + o, cmulc(wp, p));
-                if constexpr (FLAGS & RF_FORM_B) red_add_f2(a.accB + o, cmulc(wp, z));
+                const float2 yv = ld_plain(a.psiy + o);
+                const float2 z = cadd(cmul(wf, yv), a.c[e]);
+                const float2 wr = cmul(wp, cscale(yv, ib));      // w . rho
+                red_add_f2(a.accA + o, cmulc(wp, csub(p, wr)));
+                if constexpr (FLAGS & RF_FORM_B) red_add_f2(a.accB + o, cmulc(wp, csub(z, wr)));
                 const float2 cn = make_float2(fmaf(cp, p.x, b * z.x), fmaf(cp, p.y, b * z.y));
                 a.c[e] = cn;
                 if (a.write_e) a.ebuf[e] = csub(cn, z);

@@ -136,18 +136,30 @@ __global__ void q_gather_kernel(const int32_t* __restrict__ pos, const float2* _
 }
 
 // ------------------------------------------------------------------ RAAR image pass
-// psi_y = (2b A - b B) / D ; psi = A / D ; B <- 0 (it becomes the next A).
-__global__ void normalise_kernel(const float2* __restrict__ A, float2* __restrict__ B,
+// With rho = psi_y / b and the delta sums R_A = A - D rho, R_B = B - D rho:
+//   A/D = rho + R_A/D;  B/D = rho + R_B/D after a probe change, else the
+//   previous object psi (Q* z = this step's entering A);
+//   psi <- A/D;  psi_y <- 2b A/D - b B/D;  0 where D is below the threshold;
+//   R_A, R_B <- 0 for the next step.
+__global__ void normalise_kernel(float2* __restrict__ RA, float2* __restrict__ RB,
                                  const float* __restrict__ invD, float2* __restrict__ psiy,
-                                 float2* __restrict__ psi, float beta, int n) {
+                                 float2* __restrict__ psi, float beta, int form_b, int n) {
+    const float ib = 1.f / beta;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float2 a = A[i];
-        const float2 b = B[i];
         const float id = invD[i];
-        const float ka = 2.f * beta * id, kb = beta * id;
-        psiy[i] = make_float2(fmaf(ka, a.x, -kb * b.x), fmaf(ka, a.y, -kb * b.y));
-        psi[i] = cscale(a, id);
-        B[i] = make_float2(0.f, 0.f);
+        const float2 ra = RA[i];
+        float2 ny_ = make_float2(0.f, 0.f), np_ = make_float2(0.f, 0.f);
+        if (id > 0.f) {
+            const float2 rho = cscale(psiy[i], ib);
+            const float2 an = cadd(rho, cscale(ra, id));
+            const float2 bn = form_b ? cadd(rho, cscale(RB[i], id)) : psi[i];
+            np_ = an;
+            ny_ = make_float2(fmaf(2.f * beta, an.x, -beta * bn.x), fmaf(2.f * beta, an.y, -beta * bn.y));
+        }
+        psi[i] = np_;
+        psiy[i] = ny_;
+        RA[i] = make_float2(0.f, 0.f);
+        if (form_b) RB[i] = make_float2(0.f, 0.f);
     }
 }
 
@@ -351,9 +363,9 @@ cudaError_t launch_illumination(const Plan& p, const float2* w, float* w2, float
     return cudaGetLastError();
 }
 
-cudaError_t launch_normalise(Plan& p, float2* psiy, float2* psi, cudaStream_t s) {
+cudaError_t launch_normalise(Plan& p, float2* psiy, float2* psi, int form_b, cudaStream_t s) {
     const int n = p.ny * p.nx;
-    normalise_kernel<<<grid_for(n, 256), 256, 0, s>>>(p.accA, p.accB, p.invD, psiy, psi, p.prm.beta, n);
+    normalise_kernel<<<grid_for(n, 256), 256, 0, s>>>(p.accA, p.accB, p.invD, psiy, psi, p.prm.beta, form_b, n);
     return cudaGetLastError();
 }
 

@@ -329,7 +329,7 @@ int sharp_raar_init(sharp_plan plan, const float2* psi0, const float2* probe0, f
     if (psi != psi0) SHARP_CK(cudaMemcpyAsync(psi, psi0, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     SHARP_CK(cudaMemsetAsync(p.accA, 0, n * sizeof(float2), s));
     SHARP_CK(cudaMemsetAsync(p.accB, 0, n * sizeof(float2), s));
-    p.b_valid = false;
+    p.b_valid = true;   // z^(0) = Q psi0, so Q* z^(0) / D = psi0 = psi
     p.form_differs = false;
     p.e_written_iter = 0;
     p.last_iter = 0;
@@ -379,9 +379,9 @@ int sharp_raar_step(sharp_plan plan, float2* state_c, float2* psi_y, float2* psi
     a.read_e = read_e;
     a.write_e = write_e ? 1 : 0;
     SHARP_CK(timed(p, K_FRAME, 1, s, [&] { return sharp::launch_frames(sharp::MODE_RAAR, flags, a, s); }));
-    SHARP_CK(timed(p, K_IMAGE, 1, s, [&] { return sharp::launch_normalise(p, psi_y, psi, s); }));
-    std::swap(p.accA, p.accB);   // B of the next step = this step's A (= Q* z^(l))
-    p.b_valid = true;
+    const int form_b = (flags & sharp::RF_FORM_B) ? 1 : 0;
+    SHARP_CK(timed(p, K_IMAGE, 1, s, [&] { return sharp::launch_normalise(p, psi_y, psi, form_b, s); }));
+    p.b_valid = true;   // Q* z^(l) / D = psi^(l) for the next step
     if (p.form_differs) {
         SHARP_CK(cudaMemcpyAsync(p.w_form, p.w_cur, mm * sizeof(float2), cudaMemcpyDeviceToDevice, s));
         p.form_differs = false;

@@ -86,10 +86,11 @@ struct Plan {
     float* Dsum;             // Q*Q (ny*nx), FP32 compensated sum
     float* invD;             // 1/D or 0 below the threshold
     unsigned* dmax_bits;     // max D as float bits
-    // overlap accumulators (float2 images); A = Q* P_a z, B = Q* z
+    // overlap delta sums (float2 images): A = Q* P_a z = D rho + accA and
+    // B = Q* z = D rho + accB with rho = psi_y / beta
     float2* accA;
     float2* accB;
-    bool b_valid;            // B == Q* z of the entering iterate
+    bool b_valid;            // B/D equals the previous object (no probe change)
     bool initialised;
     // eps_Delta support: e = c^(l) - z^(l-1)
     float2* ebuf;            // K*m*m or nullptr
@@ -160,7 +161,7 @@ inline cudaError_t launch_frames(int mode, int flags, const FrameArgs& a, cudaSt
 // ------------------------------------------------ launchers (image_kernels.cu)
 cudaError_t launch_illumination(const Plan& p, const float2* w, float* w2, float* D, float* invD,
                                 unsigned* dmax_bits, cudaStream_t s);   // D = Q*Q of w, invD
-cudaError_t launch_normalise(Plan& p, float2* psiy, float2* psi, cudaStream_t s);
+cudaError_t launch_normalise(Plan& p, float2* psiy, float2* psi, int form_b, cudaStream_t s);
 cudaError_t launch_q_gather(const Plan& p, const float2* obj, const float2* probe, float2* frames,
                             cudaStream_t s);
 cudaError_t launch_overlap_gather(const Plan& p, const float2* probe, const float2* z, float2* img,
