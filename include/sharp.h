@@ -192,6 +192,13 @@ int sharp_amp_loss_backward(sharp_plan plan, const float2* obj, const float2* pr
                             float2* g_probe, cudaStream_t stream);
 
 /*
+ * Synchronise `stream` and report a sticky device-side failure of the plan's
+ * kernels: SHARP_ERR_TIMEOUT when a bounded wait for a bulk copy gave up
+ * (the affected step's results are invalid).  Clears the flag.
+ */
+int sharp_plan_status(sharp_plan plan, cudaStream_t stream);
+
+/*
  * Kernel timing (tracing aid; the paper reports per-kernel time shares in the
  * Fig. 3 caption).  When enabled, every kernel launch of the plan is bracketed
  * by CUDA events on the launching stream, classified as

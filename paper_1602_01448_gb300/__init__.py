@@ -20,7 +20,7 @@ __all__ = [
     "sharp_overlap_project", "sharp_probe_update", "sharp_raar_init", "sharp_raar_step",
     "sharp_solution_error", "sharp_forward_amplitudes", "sharp_amp_loss",
     "sharp_amp_loss_backward", "AmpLoss", "amp_loss", "sharp_plan_set_profiling",
-    "sharp_plan_kernel_times",
+    "sharp_plan_kernel_times", "sharp_plan_status",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -75,6 +75,7 @@ _lib_fns = {
     "sharp_amp_loss": ([_P, _P, _P, _P, _P, _P], _I),
     "sharp_amp_loss_backward": ([_P, _P, _P, _P, _D, _P, _P, _P], _I),
     "sharp_plan_set_profiling": ([_P, _I], _I),
+    "sharp_plan_status": ([_P, _P], _I),
     "sharp_plan_kernel_times": ([_P, _P, _P], _I),
 }
 _C = {name: _decl(name, *sig) for name, sig in _lib_fns.items()}
@@ -190,6 +191,11 @@ def sharp_amp_loss_backward(plan, obj, probe, amp, grad_scale, g_obj, g_probe=No
 
 
 KCLASSES = ("frame", "image", "probe", "illum", "other")
+
+
+def sharp_plan_status(plan, stream=None) -> None:
+    """Synchronise the stream; raise SharpError if a kernel flagged a failure."""
+    _check(_C["sharp_plan_status"](plan, _stream(stream)))
 
 
 def sharp_plan_set_profiling(plan, enable: bool) -> None:

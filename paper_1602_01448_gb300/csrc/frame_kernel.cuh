@@ -1,5 +1,8 @@
-// Per-frame kernels: one thread block transforms one m x m frame in registers
-// and shared memory (fft_frame.cuh).  The RAAR variant fuses, for frame i,
+// Per-frame kernels for the standalone operators: one thread block transforms
+// one m x m frame in registers and shared memory (fft_frame.cuh).  Modes: the
+// data projection P_a (Eq. 7) of explicit frames, the forward model (Eq. 1),
+// the amplitude loss and its adjoint.  The fused RAAR step lives in
+// raar_kernel.cuh.  (Earlier design notes, kept for the algebra:) for frame i,
 //   z_i = w_f . psi_y(r + x_i) + c_i                  (implicit iterate, split Q: Sec. 2.1)
 //   Z = F z_i;  Z' = a_i Z/|Z|;  p_i = F* Z'           (P_a, Eq. 7)
 //   R_A(r + x_i) += conj(w) (p_i - w rho)  [R_B += conj(w) (z_i - w rho)]   (Q*, Eqs. 8-9)
@@ -16,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "fft_frame.cuh"
+#include "raar_kernel.cuh"
 #include "sharp_common.cuh"
 
 namespace sharp {
@@ -63,23 +67,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a
         float2 v[32];
 
         // ------------------------------------------------ form the frame
-        if constexpr (MODE == MODE_RAAR) {
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                const int y = q + TX * k;
-                const int o = obj_index(py, px, y, x, a.ny, a.nx, a.wrap);
-                const float2 wf = ld_plain(a.w_form + y * M + x);
-                const float2 py_ = ld_plain(a.psiy + o);
-                const float2 z = cadd(cmul(wf, py_), a.c[fo + y * M + x]);
-                v[k] = z;
-                acc[2] += cabs2(z);
-                if ((k % CHUNK) == CHUNK - 1) chunk_fence();
-                if constexpr (FLAGS & RF_METRIC) {
-                    acc[3] += cabs2(csub(cmul(wf, ld_plain(a.psi + o)), z));
-                    if (a.read_e) acc[4] += cabs2(cadd(cmul(wf, py_), a.ebuf[fo + y * M + x]));
-                }
-            }
-        } else if constexpr (MODE == MODE_PROJECT) {
+        if constexpr (MODE == MODE_PROJECT) {
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
                 const int y = q + TX * k;
@@ -116,8 +104,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a
                     const float av = __ldg(ai + ky * M + kx);
                     const float d = av - mag;
                     acc[0] += d * d;
-                    if constexpr (MODE == MODE_RAAR) acc[1] += av * av;
-                    if constexpr (MODE == MODE_RAAR || MODE == MODE_PROJECT) {
+                    if constexpr (MODE == MODE_PROJECT) {
                         // Z'' = (a Z/|Z|) / m so that the raw inverse gives P_a z
                         X = m2 > 0.f ? cscale(X, av * inv_m * rs) : make_float2(av * inv_m, 0.f);
                     } else if constexpr (MODE == MODE_GRAD) {
@@ -132,30 +119,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a
         G::inverse(v, S, tw);
 
         // ------------------------------------------------ epilogue
-        if constexpr (MODE == MODE_RAAR) {
-            const float b = a.beta;
-            const float cp = 1.f - 2.f * b;
-            const float ib = 1.f / b;
-            const int epy = pin(py), epx = pin(px), enx = pin(a.nx);
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                const int y = q + TX * k;
-                const int o = obj_index(epy, epx, y, x, a.ny, enx, a.wrap);
-                const float2 p = v[k];
-                const float2 wf = ld_plain(a.w_form + y * M + x);
-                const float2 wp = ld_plain(a.w_proj + y * M + x);
-                const size_t e = (size_t)pin(i) * MM + y * M + x;
-                const float2 yv = ld_plain(a.psiy + o);
-                const float2 z = cadd(cmul(wf, yv), a.c[e]);
-                const float2 wr = cmul(wp, cscale(yv, ib));      // w . rho
-                red_add_f2(a.accA + o, cmulc(wp, csub(p, wr)));
-                if constexpr (FLAGS & RF_FORM_B) red_add_f2(a.accB + o, cmulc(wp, csub(z, wr)));
-                const float2 cn = make_float2(fmaf(cp, p.x, b * z.x), fmaf(cp, p.y, b * z.y));
-                a.c[e] = cn;
-                if (a.write_e) a.ebuf[e] = csub(cn, z);
-                if ((k % CHUNK) == CHUNK - 1) chunk_fence();
-            }
-        } else if constexpr (MODE == MODE_PROJECT) {
+        if constexpr (MODE == MODE_PROJECT) {
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
                 const int y = q + TX * k;
@@ -179,12 +143,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a
 
     block_sum<NT, 5>(acc, red);
     if (tid == 0) {
-        if constexpr (MODE == MODE_RAAR) {
-#pragma unroll
-            for (int j = 0; j < 5; ++j) atomicAdd(a.sums + j, (double)acc[j]);
-        } else if constexpr (MODE != MODE_AMPS) {
-            atomicAdd(a.sums, (double)acc[0]);
-        }
+        if constexpr (MODE != MODE_AMPS) atomicAdd(a.sums, (double)acc[0]);
     }
 }
 
@@ -207,13 +166,7 @@ cudaError_t launch_frames_m(int mode, int flags, const FrameArgs& a, cudaStream_
         case MODE_AMPS: return launch_one<M, MODE_AMPS, 0>(a, s);
         case MODE_LOSS: return launch_one<M, MODE_LOSS, 0>(a, s);
         case MODE_GRAD: return launch_one<M, MODE_GRAD, 0>(a, s);
-        case MODE_RAAR:
-            switch (flags & (RF_FORM_B | RF_METRIC)) {
-                case 0: return launch_one<M, MODE_RAAR, 0>(a, s);
-                case RF_FORM_B: return launch_one<M, MODE_RAAR, RF_FORM_B>(a, s);
-                case RF_METRIC: return launch_one<M, MODE_RAAR, RF_METRIC>(a, s);
-                default: return launch_one<M, MODE_RAAR, RF_FORM_B | RF_METRIC>(a, s);
-            }
+        case MODE_RAAR: return launch_raar_m<M>(flags, a, s);
     }
     return cudaErrorInvalidValue;
 }

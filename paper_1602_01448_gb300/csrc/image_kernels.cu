@@ -136,30 +136,29 @@ __global__ void q_gather_kernel(const int32_t* __restrict__ pos, const float2* _
 }
 
 // ------------------------------------------------------------------ RAAR image pass
-// With rho = psi_y / b and the delta sums R_A = A - D rho, R_B = B - D rho:
-//   A/D = rho + R_A/D;  B/D = rho + R_B/D after a probe change, else the
-//   previous object psi (Q* z = this step's entering A);
-//   psi <- A/D;  psi_y <- 2b A/D - b B/D;  0 where D is below the threshold;
-//   R_A, R_B <- 0 for the next step.
-__global__ void normalise_kernel(float2* __restrict__ RA, float2* __restrict__ RB,
+// The frame pass scattered C = Q* c_new = (1-2b) A + b B (and B = Q* z after a
+// probe change).  Per pixel with D above the threshold:
+//   B/D = accB/D after a probe change, else the previous object psi;
+//   A/D = (C/D - b B/D) / (1-2b);  psi <- A/D;  psi_y <- 2b A/D - b B/D;
+// both 0 below the threshold; the sums are cleared for the next step.
+__global__ void normalise_kernel(float2* __restrict__ C, float2* __restrict__ B,
                                  const float* __restrict__ invD, float2* __restrict__ psiy,
                                  float2* __restrict__ psi, float beta, int form_b, int n) {
-    const float ib = 1.f / beta;
+    const float k = 1.f / (1.f - 2.f * beta);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float id = invD[i];
-        const float2 ra = RA[i];
+        const float2 cs = C[i];
         float2 ny_ = make_float2(0.f, 0.f), np_ = make_float2(0.f, 0.f);
         if (id > 0.f) {
-            const float2 rho = cscale(psiy[i], ib);
-            const float2 an = cadd(rho, cscale(ra, id));
-            const float2 bn = form_b ? cadd(rho, cscale(RB[i], id)) : psi[i];
+            const float2 bn = form_b ? cscale(B[i], id) : psi[i];
+            const float2 an = make_float2(k * fmaf(cs.x, id, -beta * bn.x), k * fmaf(cs.y, id, -beta * bn.y));
             np_ = an;
             ny_ = make_float2(fmaf(2.f * beta, an.x, -beta * bn.x), fmaf(2.f * beta, an.y, -beta * bn.y));
         }
         psi[i] = np_;
         psiy[i] = ny_;
-        RA[i] = make_float2(0.f, 0.f);
-        if (form_b) RB[i] = make_float2(0.f, 0.f);
+        C[i] = make_float2(0.f, 0.f);
+        if (form_b) B[i] = make_float2(0.f, 0.f);
     }
 }
 

@@ -1,0 +1,240 @@
+// Persistent fused RAAR frame pass (Sec. 2.2 RAAR update, Eqs. 5, 7-9).
+//
+// For frame i with state c_i and measured amplitudes a_i:
+//   z   = w_f . psi_y(r + x_i) + c_i                      split Q (Eq. 5)
+//   Z   = F z                                             Eq. 2
+//   Z'  = a Z/|Z|                                         P_a (Eq. 7); eps_a partials
+//   c_i <- F* [(1-2b) Z' + b Z] = (1-2b) P_a z + b z       RAAR state
+//   C(r + x_i) += conj(w) c_i                             Q* of the new state
+// Because c_new = (1-2b) P_a z + b z, Q* c_new = (1-2b) A + b B with
+// A = Q* P_a z and B = Q* z, so the image pass recovers A = (C - b B)/(1-2b)
+// and forms psi = A/D, psi_y = (2b A - b B)/D; B/D is the previous object
+// unless the probe changed (then B is scattered here from z).  Transforming
+// the combination instead of Z' alone means the epilogue needs neither the old
+// state nor a second gather: each frame is read once and written once.
+//
+// One persistent block per SM walks frames i = blockIdx.x + k * gridDim.x.
+// Frame i+1's state is copied by TMA (cp.async.bulk) into the FFT exchange
+// buffer while frame i finishes its epilogue, and its amplitudes into a padded
+// staging buffer while frame i runs its inverse transform; completion is
+// tracked by two mbarriers with bounded waits.
+#pragma once
+
+#include "fft_frame.cuh"
+#include "sharp_common.cuh"
+#include "tma.cuh"
+
+namespace sharp {
+
+template <int M>
+struct RaarGeo {
+    using G = Fft3<M>;
+    // row pitch (floats) of the amplitude staging buffer: conflict-free for the
+    // pass-3 read pattern (TT consecutive columns x 32/TT rows per warp) and a
+    // multiple of 16 bytes for the per-row bulk copies
+    static constexpr int APITCH = (M == 128) ? 136 : 80;
+    static constexpr size_t S_BYTES = sizeof(float2) * G::SMEM_ELEMS;
+    static constexpr size_t TW_BYTES = sizeof(float2) * (G::TW1 + G::TW2);
+    static constexpr size_t A_BYTES = sizeof(float) * M * APITCH;
+    static constexpr size_t SMEM = S_BYTES + TW_BYTES + A_BYTES + 2 * sizeof(uint64_t);
+    static_assert(S_BYTES >= sizeof(float2) * M * M, "state staging must fit the exchange buffer");
+    static_assert((S_BYTES + TW_BYTES + A_BYTES) % 8 == 0, "mbarrier alignment");
+};
+
+__device__ __forceinline__ void chunk_fence_r() { asm volatile("" ::: "memory"); }
+
+template <class T>
+__device__ __forceinline__ T ldg_plain(const T* p) { return *p; }
+
+template <int M, int FLAGS, int WRAP>
+__global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(const FrameArgs a) {
+    using G = Fft3<M>;
+    using R = RaarGeo<M>;
+    constexpr int NT = G::NT;
+    constexpr int TX = G::TX;
+    constexpr int MM = M * M;
+    constexpr int CH = 8;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2* S = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = reinterpret_cast<float2*>(smem_raw + R::S_BYTES);
+    float* ast = reinterpret_cast<float*>(smem_raw + R::S_BYTES + R::TW_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + R::S_BYTES + R::TW_BYTES + R::A_BYTES);
+    __shared__ float red[32 * 5];
+
+    const int tid = threadIdx.x;
+    const int q = tid / M;
+    const int x = tid % M;
+    const float inv_m = 1.0f / M;
+    const float b = a.beta;
+    const float cp = 1.f - 2.f * b;
+
+    if ((int)blockIdx.x >= a.K) return;
+    G::load_twiddles(tw);
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    auto issue_c = [&](int f) {
+        mbar_expect_tx(&bars[0], (unsigned)(MM * sizeof(float2)));
+        bulk_g2s(S, a.c + (size_t)f * MM, (unsigned)(MM * sizeof(float2)), &bars[0]);
+    };
+    auto issue_a = [&](int f) {
+        mbar_expect_tx(&bars[1], (unsigned)(MM * sizeof(float)));
+        const float* src = a.amp + (size_t)f * MM;
+        for (int r = 0; r < M; ++r) bulk_g2s(ast + r * R::APITCH, src + r * M, (unsigned)(M * sizeof(float)), &bars[1]);
+    };
+    if (tid == 0) {
+        issue_c(blockIdx.x);
+        issue_a(blockIdx.x);
+    }
+
+    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    unsigned par_c = 0, par_a = 0;
+    bool c_pending = true, a_pending = true;   // uniform across the block
+    bool ok = true;
+
+    for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
+        const int nxt = i + gridDim.x;
+        const int py = a.pos[2 * i];
+        const int px = a.pos[2 * i + 1];
+        const size_t fo = (size_t)i * MM;
+        float2 v[32];
+
+        // ---------------------------------------------- state arrives (TMA)
+        ok = __syncthreads_and(mbar_wait(&bars[0], par_c));
+        if (!ok) break;
+        par_c ^= 1u;
+        c_pending = false;
+
+        // ---------------------------------------------- z = w_f . psi_y + c
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const int y = q + TX * k;
+            const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
+            const float2 wf = ldg_plain(a.w_form + y * M + x);
+            const float2 yv = ldg_plain(a.psiy + o);
+            const float2 z = cadd(cmul(wf, yv), S[y * M + x]);
+            v[k] = z;
+            acc[2] += cabs2(z);
+            if constexpr (FLAGS & RF_METRIC) {
+                acc[3] += cabs2(csub(cmul(wf, ldg_plain(a.psi + o)), z));
+                if (a.read_e) acc[4] += cabs2(cadd(cmul(wf, yv), ldg_plain(a.ebuf + fo + y * M + x)));
+            }
+            if constexpr (FLAGS & RF_FORM_B) red_add_f2(a.accB + o, cmulc(ldg_plain(a.w_proj + y * M + x), z));
+            if (a.write_e) a.ebuf[fo + y * M + x] = make_float2(-z.x, -z.y);
+            if ((k % CH) == CH - 1) chunk_fence_r();
+        }
+
+        G::forward(v, S, tw);
+
+        // ---------------------------------------------- amplitudes arrive (TMA)
+        ok = __syncthreads_and(mbar_wait(&bars[1], par_a));
+        if (!ok) break;
+        par_a ^= 1u;
+        a_pending = false;
+
+        // ---------------------------------------------- Fourier domain
+        // Y = ((1-2b) a Z/|Z| + b Z) / m on the unitary scale, so the raw
+        // inverse returns c_new directly; phase 1 where Z = 0.
+#pragma unroll
+        for (int c = 0; c < G::C3; ++c) {
+            const int ky = G::p3_ky(c);
+#pragma unroll
+            for (int s = 0; s < G::X0; ++s) {
+                const int kx = G::p3_kx(s);
+                float2& X = v[c * G::X0 + s];
+                const float av = ast[ky * R::APITCH + kx];
+                const float m2 = cabs2(X);
+                const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
+                const float d = av - m2 * rs * inv_m;
+                acc[0] += d * d;
+                acc[1] += av * av;
+                X = m2 > 0.f ? cscale(X, fmaf(cp * av, rs, b * inv_m) * inv_m)
+                             : make_float2(cp * av * inv_m, 0.f);
+            }
+        }
+        fence_proxy_async_smem();
+        __syncthreads();                       // amplitude buffer free
+        if (nxt < a.K) {
+            if (tid == 0) issue_a(nxt);
+            a_pending = true;
+        }
+
+        G::inverse(v, S, tw);
+
+        fence_proxy_async_smem();
+        __syncthreads();                       // exchange buffer free
+        if (nxt < a.K) {
+            if (tid == 0) issue_c(nxt);
+            c_pending = true;
+        }
+
+        // ---------------------------------------------- epilogue: store, scatter
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const int y = q + TX * k;
+            const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
+            const float2 cn = v[k];
+            a.c[fo + y * M + x] = cn;
+            red_add_f2(a.accA + o, cmulc(ldg_plain(a.w_proj + y * M + x), cn));
+            if (a.write_e) red_add_f2(a.ebuf + fo + y * M + x, cn);
+            if ((k % CH) == CH - 1) chunk_fence_r();
+        }
+    }
+
+    if (!ok) {
+        // A wait gave up: drain (bounded) whatever copies this block may still
+        // have in flight, flag the failure, and leave the sums alone.
+        if (c_pending) mbar_wait(&bars[0], par_c);
+        if (a_pending) mbar_wait(&bars[1], par_a);
+        if (tid == 0) atomicExch(a.err, SHARP_ERR_TIMEOUT);
+        return;
+    }
+    block_sum<NT, 5>(acc, red);
+    if (tid == 0) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) atomicAdd(a.sums + j, (double)acc[j]);
+    }
+}
+
+template <int M, int FLAGS, int WRAP>
+static cudaError_t launch_raar_one(const FrameArgs& a, cudaStream_t s) {
+    using R = RaarGeo<M>;
+    auto kern = raar_kernel<M, FLAGS, WRAP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Fft3<M>::NT, R::SMEM)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int grid = sms * per_sm;
+    if (grid > a.K) grid = a.K;
+    kern<<<grid, Fft3<M>::NT, R::SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_raar_m(int flags, const FrameArgs& a, cudaStream_t s) {
+    const int f = flags & (RF_FORM_B | RF_METRIC);
+    if (a.wrap) {
+        switch (f) {
+            case 0: return launch_raar_one<M, 0, 1>(a, s);
+            case RF_FORM_B: return launch_raar_one<M, RF_FORM_B, 1>(a, s);
+            case RF_METRIC: return launch_raar_one<M, RF_METRIC, 1>(a, s);
+            default: return launch_raar_one<M, RF_FORM_B | RF_METRIC, 1>(a, s);
+        }
+    }
+    switch (f) {
+        case 0: return launch_raar_one<M, 0, 0>(a, s);
+        case RF_FORM_B: return launch_raar_one<M, RF_FORM_B, 0>(a, s);
+        case RF_METRIC: return launch_raar_one<M, RF_METRIC, 0>(a, s);
+        default: return launch_raar_one<M, RF_FORM_B | RF_METRIC, 0>(a, s);
+    }
+}
+
+}  // namespace sharp

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -83,7 +84,7 @@ void free_plan(Plan& p) {
     void* ptrs[] = {p.pos,   p.tile_ptr,   p.tile_frames, p.w_cur, p.w_form,     p.w2,
                     p.Dsum,  p.invD,       p.dmax_bits,   p.accA,  p.accB,       p.ebuf,
                     p.sums,  p.probe_part, p.probe_acc,   p.scal,  p.w2tmp,      p.Dtmp,
-                    p.invDtmp};
+                    p.invDtmp, p.errflag};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     std::memset(&p, 0, sizeof(p));
@@ -100,6 +101,7 @@ sharp::FrameArgs base_args(const Plan& p) {
     a.pos = p.pos;
     a.beta = p.prm.beta;
     a.sums = p.sums;
+    a.err = p.errflag;
     return a;
 }
 
@@ -208,11 +210,13 @@ int sharp_plan_create(sharp_plan* out, int K, int m, int ny, int nx, const int32
     SHARP_ALLOC(w2tmp, mm)
     SHARP_ALLOC(Dtmp, n)
     SHARP_ALLOC(invDtmp, n)
+    SHARP_ALLOC(errflag, 1)
 #undef SHARP_ALLOC
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.pos, hpos.data(), hpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.tile_ptr, count.data(), count.size() * sizeof(int), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(p.tile_frames, frames.data(), (size_t)nnz * sizeof(int), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p.scal, 0, 32 * sizeof(double), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.errflag, 0, sizeof(int), stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // host vectors die here
     if (e != cudaSuccess) {
         free_plan(p);
@@ -220,6 +224,18 @@ int sharp_plan_create(sharp_plan* out, int K, int m, int ny, int nx, const int32
         return fail(SHARP_ERR_CUDA, "plan allocation: %s", cudaGetErrorString(e));
     }
     *out = h;
+    return SHARP_OK;
+}
+
+int sharp_plan_status(sharp_plan plan, cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    int flag = 0;
+    SHARP_CK(cudaMemcpyAsync(&flag, plan->p.errflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SHARP_CK(cudaStreamSynchronize(s));
+    if (flag != 0) {
+        SHARP_CK(cudaMemsetAsync(plan->p.errflag, 0, sizeof(int), s));
+        return fail(flag, "a bounded device-side wait gave up (the step's results are invalid)");
+    }
     return SHARP_OK;
 }
 
@@ -343,6 +359,8 @@ int sharp_raar_step(sharp_plan plan, float2* state_c, float2* psi_y, float2* psi
     SHARP_NONNULL(state_c); SHARP_NONNULL(psi_y); SHARP_NONNULL(psi); SHARP_NONNULL(amp);
     Plan& p = plan->p;
     if (!p.initialised) return fail(SHARP_ERR_STATE, "sharp_raar_step before sharp_raar_init");
+    if ((reinterpret_cast<uintptr_t>(state_c) | reinterpret_cast<uintptr_t>(amp)) & 15)
+        return fail(SHARP_ERR_INVALID_ARG, "state_c and amp must be 16-byte aligned (bulk copies)");
     if (iter < 1) return fail(SHARP_ERR_INVALID_ARG, "iter = %d < 1", iter);
     const size_t mm = (size_t)p.m * p.m;
     const int R = p.prm.residual_every;

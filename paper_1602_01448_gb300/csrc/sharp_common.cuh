@@ -86,8 +86,8 @@ struct Plan {
     float* Dsum;             // Q*Q (ny*nx), FP32 compensated sum
     float* invD;             // 1/D or 0 below the threshold
     unsigned* dmax_bits;     // max D as float bits
-    // overlap delta sums (float2 images): A = Q* P_a z = D rho + accA and
-    // B = Q* z = D rho + accB with rho = psi_y / beta
+    // overlap sums (float2 images): accA = Q* c_new (c_new the new frame
+    // state), accB = Q* z (only after a probe change)
     float2* accA;
     float2* accB;
     bool b_valid;            // B/D equals the previous object (no probe change)
@@ -108,6 +108,7 @@ struct Plan {
     float* invDtmp;          // ny*nx
     bool form_differs;       // w_form != w_cur (a probe update happened)
     void* prof;              // kernel-timing state (sharp_api.cu), nullptr when off
+    int* errflag;            // device int: sticky error raised inside kernels
 };
 
 constexpr int TILE = 32;
@@ -141,6 +142,7 @@ struct FrameArgs {
     float2* g_probe;
     float gscale;
     double* sums;            // per-mode accumulators
+    int* err;                // device error flag (SHARP_ERR_TIMEOUT on a bounded-wait failure)
 };
 
 // compile-time flags of MODE_RAAR
@@ -148,6 +150,8 @@ enum RaarFlags { RF_FORM_B = 1, RF_METRIC = 2 };
 
 template <int M>
 cudaError_t launch_frames_m(int mode, int flags, const FrameArgs& a, cudaStream_t s);
+template <int M>
+cudaError_t launch_raar_m(int flags, const FrameArgs& a, cudaStream_t s);
 
 inline cudaError_t launch_frames(int mode, int flags, const FrameArgs& a, cudaStream_t s) {
     if (a.K <= 0) return cudaSuccess;
