@@ -19,7 +19,6 @@
 #include <cuda_runtime.h>
 
 #include "fft_frame.cuh"
-#include "raar_kernel.cuh"
 #include "sharp_common.cuh"
 
 namespace sharp {

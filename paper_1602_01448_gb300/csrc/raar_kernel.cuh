@@ -218,22 +218,14 @@ static cudaError_t launch_raar_one(const FrameArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int M>
-cudaError_t launch_raar_m(int flags, const FrameArgs& a, cudaStream_t s) {
-    const int f = flags & (RF_FORM_B | RF_METRIC);
-    if (a.wrap) {
-        switch (f) {
-            case 0: return launch_raar_one<M, 0, 1>(a, s);
-            case RF_FORM_B: return launch_raar_one<M, RF_FORM_B, 1>(a, s);
-            case RF_METRIC: return launch_raar_one<M, RF_METRIC, 1>(a, s);
-            default: return launch_raar_one<M, RF_FORM_B | RF_METRIC, 1>(a, s);
-        }
-    }
-    switch (f) {
-        case 0: return launch_raar_one<M, 0, 0>(a, s);
-        case RF_FORM_B: return launch_raar_one<M, RF_FORM_B, 0>(a, s);
-        case RF_METRIC: return launch_raar_one<M, RF_METRIC, 0>(a, s);
-        default: return launch_raar_one<M, RF_FORM_B | RF_METRIC, 0>(a, s);
+// All flag variants of one (frame size, wrap) pair; one translation unit each.
+template <int M, int WRAP>
+cudaError_t launch_raar_w(int flags, const FrameArgs& a, cudaStream_t s) {
+    switch (flags & (RF_FORM_B | RF_METRIC)) {
+        case 0: return launch_raar_one<M, 0, WRAP>(a, s);
+        case RF_FORM_B: return launch_raar_one<M, RF_FORM_B, WRAP>(a, s);
+        case RF_METRIC: return launch_raar_one<M, RF_METRIC, WRAP>(a, s);
+        default: return launch_raar_one<M, RF_FORM_B | RF_METRIC, WRAP>(a, s);
     }
 }
 

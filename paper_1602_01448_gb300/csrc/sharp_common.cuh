@@ -150,8 +150,12 @@ enum RaarFlags { RF_FORM_B = 1, RF_METRIC = 2 };
 
 template <int M>
 cudaError_t launch_frames_m(int mode, int flags, const FrameArgs& a, cudaStream_t s);
+template <int M, int WRAP>
+cudaError_t launch_raar_w(int flags, const FrameArgs& a, cudaStream_t s);
 template <int M>
-cudaError_t launch_raar_m(int flags, const FrameArgs& a, cudaStream_t s);
+inline cudaError_t launch_raar_m(int flags, const FrameArgs& a, cudaStream_t s) {
+    return a.wrap ? launch_raar_w<M, 1>(flags, a, s) : launch_raar_w<M, 0>(flags, a, s);
+}
 
 inline cudaError_t launch_frames(int mode, int flags, const FrameArgs& a, cudaStream_t s) {
     if (a.K <= 0) return cudaSuccess;
