@@ -14,10 +14,13 @@
 // state nor a second gather: each frame is read once and written once.
 //
 // One persistent block per SM walks frames i = blockIdx.x + k * gridDim.x.
-// Frame i+1's state is copied by TMA (cp.async.bulk) into the FFT exchange
-// buffer while frame i finishes its epilogue, and its amplitudes into a padded
-// staging buffer while frame i runs its inverse transform; completion is
-// tracked by two mbarriers with bounded waits.
+// Frame i+1's state is copied by TMA (one cp.async.bulk of m^2 complex values)
+// into the FFT exchange buffer while frame i finishes its epilogue; its
+// completion is tracked by an mbarrier with a bounded wait.  Each frame's
+// amplitudes are prefetched into L2 by a bulk prefetch when the frame starts
+// and read by the Fourier phase.  L2 policies keep the object, probe and
+// overlap images resident (evict_last) while the streamed state and
+// amplitudes go first (evict_first).
 #pragma once
 
 #include "fft_frame.cuh"
@@ -29,16 +32,11 @@ namespace sharp {
 template <int M>
 struct RaarGeo {
     using G = Fft3<M>;
-    // row pitch (floats) of the amplitude staging buffer: conflict-free for the
-    // pass-3 read pattern (TT consecutive columns x 32/TT rows per warp) and a
-    // multiple of 16 bytes for the per-row bulk copies
-    static constexpr int APITCH = (M == 128) ? 136 : 80;
     static constexpr size_t S_BYTES = sizeof(float2) * G::SMEM_ELEMS;
     static constexpr size_t TW_BYTES = sizeof(float2) * (G::TW1 + G::TW2);
-    static constexpr size_t A_BYTES = sizeof(float) * M * APITCH;
-    static constexpr size_t SMEM = S_BYTES + TW_BYTES + A_BYTES + 2 * sizeof(uint64_t);
+    static constexpr size_t SMEM = S_BYTES + TW_BYTES + 2 * sizeof(uint64_t);
     static_assert(S_BYTES >= sizeof(float2) * M * M, "state staging must fit the exchange buffer");
-    static_assert((S_BYTES + TW_BYTES + A_BYTES) % 8 == 0, "mbarrier alignment");
+    static_assert((S_BYTES + TW_BYTES) % 8 == 0, "mbarrier alignment");
 };
 
 __device__ __forceinline__ void chunk_fence_r() { asm volatile("" ::: "memory"); }
@@ -57,8 +55,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2* S = reinterpret_cast<float2*>(smem_raw);
     float2* tw = reinterpret_cast<float2*>(smem_raw + R::S_BYTES);
-    float* ast = reinterpret_cast<float*>(smem_raw + R::S_BYTES + R::TW_BYTES);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + R::S_BYTES + R::TW_BYTES + R::A_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + R::S_BYTES + R::TW_BYTES);
     __shared__ float red[32 * 5];
 
     const int tid = threadIdx.x;
@@ -72,28 +69,21 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
     G::load_twiddles(tw);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
         mbar_fence_init();
     }
     __syncthreads();
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
 
     auto issue_c = [&](int f) {
         mbar_expect_tx(&bars[0], (unsigned)(MM * sizeof(float2)));
-        bulk_g2s(S, a.c + (size_t)f * MM, (unsigned)(MM * sizeof(float2)), &bars[0]);
+        bulk_g2s_hint(S, a.c + (size_t)f * MM, (unsigned)(MM * sizeof(float2)), &bars[0], pol_stream);
     };
-    auto issue_a = [&](int f) {
-        mbar_expect_tx(&bars[1], (unsigned)(MM * sizeof(float)));
-        const float* src = a.amp + (size_t)f * MM;
-        for (int r = 0; r < M; ++r) bulk_g2s(ast + r * R::APITCH, src + r * M, (unsigned)(M * sizeof(float)), &bars[1]);
-    };
-    if (tid == 0) {
-        issue_c(blockIdx.x);
-        issue_a(blockIdx.x);
-    }
+    if (tid == 0) issue_c(blockIdx.x);
 
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    unsigned par_c = 0, par_a = 0;
-    bool c_pending = true, a_pending = true;   // uniform across the block
+    unsigned par_c = 0;
+    bool c_pending = true;   // uniform across the block
     bool ok = true;
 
     for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
@@ -102,6 +92,8 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
         const int px = a.pos[2 * i + 1];
         const size_t fo = (size_t)i * MM;
         float2 v[32];
+
+        if (tid == 0) bulk_prefetch_l2(a.amp + fo, (unsigned)(MM * sizeof(float)));
 
         // ---------------------------------------------- state arrives (TMA)
         ok = __syncthreads_and(mbar_wait(&bars[0], par_c));
@@ -114,31 +106,26 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
         for (int k = 0; k < 32; ++k) {
             const int y = q + TX * k;
             const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
-            const float2 wf = ldg_plain(a.w_form + y * M + x);
-            const float2 yv = ldg_plain(a.psiy + o);
+            const float2 wf = ld_hint(a.w_form + y * M + x, pol_keep);
+            const float2 yv = ld_hint(a.psiy + o, pol_keep);
             const float2 z = cadd(cmul(wf, yv), S[y * M + x]);
             v[k] = z;
             acc[2] += cabs2(z);
             if constexpr (FLAGS & RF_METRIC) {
-                acc[3] += cabs2(csub(cmul(wf, ldg_plain(a.psi + o)), z));
+                acc[3] += cabs2(csub(cmul(wf, ld_hint(a.psi + o, pol_keep)), z));
                 if (a.read_e) acc[4] += cabs2(cadd(cmul(wf, yv), ldg_plain(a.ebuf + fo + y * M + x)));
             }
-            if constexpr (FLAGS & RF_FORM_B) red_add_f2(a.accB + o, cmulc(ldg_plain(a.w_proj + y * M + x), z));
+            if constexpr (FLAGS & RF_FORM_B) red_hint(a.accB + o, cmulc(ld_hint(a.w_proj + y * M + x, pol_keep), z), pol_keep);
             if (a.write_e) a.ebuf[fo + y * M + x] = make_float2(-z.x, -z.y);
             if ((k % CH) == CH - 1) chunk_fence_r();
         }
 
         G::forward(v, S, tw);
 
-        // ---------------------------------------------- amplitudes arrive (TMA)
-        ok = __syncthreads_and(mbar_wait(&bars[1], par_a));
-        if (!ok) break;
-        par_a ^= 1u;
-        a_pending = false;
-
         // ---------------------------------------------- Fourier domain
         // Y = ((1-2b) a Z/|Z| + b Z) / m on the unitary scale, so the raw
         // inverse returns c_new directly; phase 1 where Z = 0.
+        const float* ai = a.amp + fo;
 #pragma unroll
         for (int c = 0; c < G::C3; ++c) {
             const int ky = G::p3_ky(c);
@@ -146,7 +133,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
             for (int s = 0; s < G::X0; ++s) {
                 const int kx = G::p3_kx(s);
                 float2& X = v[c * G::X0 + s];
-                const float av = ast[ky * R::APITCH + kx];
+                const float av = __ldcs(ai + ky * M + kx);   // streamed once: evict-first
                 const float m2 = cabs2(X);
                 const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
                 const float d = av - m2 * rs * inv_m;
@@ -156,13 +143,6 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
                              : make_float2(cp * av * inv_m, 0.f);
             }
         }
-        fence_proxy_async_smem();
-        __syncthreads();                       // amplitude buffer free
-        if (nxt < a.K) {
-            if (tid == 0) issue_a(nxt);
-            a_pending = true;
-        }
-
         G::inverse(v, S, tw);
 
         fence_proxy_async_smem();
@@ -178,8 +158,8 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
             const int y = q + TX * k;
             const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
             const float2 cn = v[k];
-            a.c[fo + y * M + x] = cn;
-            red_add_f2(a.accA + o, cmulc(ldg_plain(a.w_proj + y * M + x), cn));
+            st_hint(a.c + fo + y * M + x, cn, pol_stream);
+            red_hint(a.accA + o, cmulc(ld_hint(a.w_proj + y * M + x, pol_keep), cn), pol_keep);
             if (a.write_e) red_add_f2(a.ebuf + fo + y * M + x, cn);
             if ((k % CH) == CH - 1) chunk_fence_r();
         }
@@ -189,7 +169,6 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
         // A wait gave up: drain (bounded) whatever copies this block may still
         // have in flight, flag the failure, and leave the sums alone.
         if (c_pending) mbar_wait(&bars[0], par_c);
-        if (a_pending) mbar_wait(&bars[1], par_a);
         if (tid == 0) atomicExch(a.err, SHARP_ERR_TIMEOUT);
         return;
     }
