@@ -1,6 +1,6 @@
 """Benchmark: RAAR frame-iterations/s on one GB300 for the 2500-frame 128^2
 Fermat-spiral scan over a 1024^2 object (probe refinement every 2nd step,
-eps_a/eps_Q every step), with the fused frame kernel's HBM roofline fraction,
+eps_a every step, eps_Q and eps_Delta every 10th), with the fused frame kernel's HBM roofline fraction,
 an end-to-end figure through the C ABI with host buffers, and the FP64 oracle
 timed on the host cores as a reported CPU baseline.
 
@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "RAAR frame-iterations/s on 1 GB300 (FP32 vs mixed) and % of HBM roofline"
 UNIT = "frame-iterations/s"
 WORKLOAD = "fermat-2500x128-obj1024"
+RESIDUAL_EVERY = 10   # eps_Q and eps_Delta every 10th step; eps_a every step
 PROFILE = os.path.join(ROOT, "profiles", "frame_kernel_fermat2500x128.txt")
 CSRC = os.path.join(ROOT, "paper_1602_01448_gb300", "csrc")
 
@@ -185,7 +186,7 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", local)
     scan = make_scan(args.frames)
     K, m = scan.K, scan.m
-    plan = S.Plan(scan.pos, m, scan.shape, beta=0.75, probe_every=scan.probe_every, residual_every=1,
+    plan = S.Plan(scan.pos, m, scan.shape, beta=0.75, probe_every=scan.probe_every, residual_every=RESIDUAL_EVERY,
                   device=dev)
     obj = torch.as_tensor(scan.obj).to(torch.complex64).to(dev)
     probe_true = torch.as_tensor(scan.probe).to(torch.complex64).to(dev)
@@ -280,7 +281,7 @@ def run_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if K == 2500 else f"fermat-{K}x128-obj1024", "frames": K, "frame": m, "object": list(scan.shape),
-                   "beta": 0.75, "probe_every": scan.probe_every, "residual_every": 1,
+                   "beta": 0.75, "probe_every": scan.probe_every, "residual_every": RESIDUAL_EVERY,
                    "photons_per_frame": scan.photons, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (c 328 MB + a 164 MB per step)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -65,7 +65,6 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
     const float b = a.beta;
     const float cp = 1.f - 2.f * b;
 
-    if ((int)blockIdx.x >= a.K) return;
     G::load_twiddles(tw);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -79,15 +78,28 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
         mbar_expect_tx(&bars[0], (unsigned)(MM * sizeof(float2)));
         bulk_g2s_hint(S, a.c + (size_t)f * MM, (unsigned)(MM * sizeof(float2)), &bars[0], pol_stream);
     };
-    if (tid == 0) issue_c(blockIdx.x);
+    // Frames are handed out by an atomic counter.  Blocks start staggered by
+    // a fraction of a frame time so that the SMs' memory phases (gathers,
+    // scatter, state stores) interleave instead of all hitting the memory
+    // system at once.
+    __shared__ int s_next;
+    if (tid == 0) {
+        __nanosleep(2000u * (blockIdx.x & 3u));
+        const int f = atomicAdd(a.counter, 1);
+        s_next = f;
+        if (f < a.K) issue_c(f);
+    }
+    __syncthreads();
+    int cur = s_next;
 
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     unsigned par_c = 0;
-    bool c_pending = true;   // uniform across the block
+    bool c_pending = cur < a.K;   // uniform across the block
     bool ok = true;
 
-    for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
-        const int nxt = i + gridDim.x;
+    while (cur < a.K) {
+        const int i = cur;
+        if (tid == 0) s_next = atomicAdd(a.counter, 1);
         const int py = a.pos[2 * i];
         const int px = a.pos[2 * i + 1];
         const size_t fo = (size_t)i * MM;
@@ -100,24 +112,53 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
         if (!ok) break;
         par_c ^= 1u;
         c_pending = false;
+        const int nxt = s_next;   // published before the barrier above
 
         // ---------------------------------------------- z = w_f . psi_y + c
+        // Per chunk of CH rows: issue every load first, then compute, then
+        // store (a store ahead of the next row's loads would serialise them).
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            const int y = q + TX * k;
-            const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
-            const float2 wf = ld_hint(a.w_form + y * M + x, pol_keep);
-            const float2 yv = ld_hint(a.psiy + o, pol_keep);
-            const float2 z = cadd(cmul(wf, yv), S[y * M + x]);
-            v[k] = z;
-            acc[2] += cabs2(z);
-            if constexpr (FLAGS & RF_METRIC) {
-                acc[3] += cabs2(csub(cmul(wf, ld_hint(a.psi + o, pol_keep)), z));
-                if (a.read_e) acc[4] += cabs2(cadd(cmul(wf, yv), ldg_plain(a.ebuf + fo + y * M + x)));
+        for (int k0 = 0; k0 < 32; k0 += CH) {
+            float2 wf[CH], yv[CH], pv[CH], ev[CH];
+#pragma unroll
+            for (int k = k0; k < k0 + CH; ++k) {
+                const int y = q + TX * k;
+                const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
+                wf[k - k0] = ld_hint(a.w_form + y * M + x, pol_keep);
+                yv[k - k0] = ld_hint(a.psiy + o, pol_keep);
+                if constexpr (FLAGS & RF_METRIC) {
+                    pv[k - k0] = ld_hint(a.psi + o, pol_keep);
+                    ev[k - k0] = a.read_e ? ld_hint(a.ebuf + fo + y * M + x, pol_stream) : make_float2(0.f, 0.f);
+                }
             }
-            if constexpr (FLAGS & RF_FORM_B) red_hint(a.accB + o, cmulc(ld_hint(a.w_proj + y * M + x, pol_keep), z), pol_keep);
-            if (a.write_e) a.ebuf[fo + y * M + x] = make_float2(-z.x, -z.y);
-            if ((k % CH) == CH - 1) chunk_fence_r();
+#pragma unroll
+            for (int k = k0; k < k0 + CH; ++k) {
+                const int y = q + TX * k;
+                const float2 wy = cmul(wf[k - k0], yv[k - k0]);
+                const float2 z = cadd(wy, S[y * M + x]);
+                v[k] = z;
+                acc[2] += cabs2(z);
+                if constexpr (FLAGS & RF_METRIC) {
+                    acc[3] += cabs2(csub(cmul(wf[k - k0], pv[k - k0]), z));
+                    acc[4] += cabs2(cadd(wy, ev[k - k0]));
+                }
+            }
+            if constexpr (FLAGS & RF_FORM_B) {
+#pragma unroll
+                for (int k = k0; k < k0 + CH; ++k) {
+                    const int y = q + TX * k;
+                    const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
+                    red_hint(a.accB + o, cmulc(ld_hint(a.w_proj + y * M + x, pol_keep), v[k]), pol_keep);
+                }
+            }
+            if (a.write_e) {
+#pragma unroll
+                for (int k = k0; k < k0 + CH; ++k) {
+                    const int y = q + TX * k;
+                    st_hint(a.ebuf + fo + y * M + x, make_float2(-v[k].x, -v[k].y), pol_stream);
+                }
+            }
+            chunk_fence_r();
         }
 
         G::forward(v, S, tw);
@@ -154,15 +195,22 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
 
         // ---------------------------------------------- epilogue: store, scatter
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            const int y = q + TX * k;
-            const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
-            const float2 cn = v[k];
-            st_hint(a.c + fo + y * M + x, cn, pol_stream);
-            red_hint(a.accA + o, cmulc(ld_hint(a.w_proj + y * M + x, pol_keep), cn), pol_keep);
-            if (a.write_e) red_add_f2(a.ebuf + fo + y * M + x, cn);
-            if ((k % CH) == CH - 1) chunk_fence_r();
+        for (int k0 = 0; k0 < 32; k0 += CH) {
+            float2 wp[CH];
+#pragma unroll
+            for (int k = k0; k < k0 + CH; ++k) wp[k - k0] = ld_hint(a.w_proj + (q + TX * k) * M + x, pol_keep);
+#pragma unroll
+            for (int k = k0; k < k0 + CH; ++k) {
+                const int y = q + TX * k;
+                const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
+                const float2 cn = v[k];
+                st_hint(a.c + fo + y * M + x, cn, pol_stream);
+                red_hint(a.accA + o, cmulc(wp[k - k0], cn), pol_keep);
+                if (a.write_e) red_hint(a.ebuf + fo + y * M + x, cn, pol_stream);
+            }
+            chunk_fence_r();
         }
+        cur = nxt;
     }
 
     if (!ok) {
@@ -193,6 +241,7 @@ static cudaError_t launch_raar_one(const FrameArgs& a, cudaStream_t s) {
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = sms * per_sm;
     if (grid > a.K) grid = a.K;
+    if ((e = cudaMemsetAsync(a.counter, 0, sizeof(int), s)) != cudaSuccess) return e;
     kern<<<grid, Fft3<M>::NT, R::SMEM, s>>>(a);
     return cudaGetLastError();
 }

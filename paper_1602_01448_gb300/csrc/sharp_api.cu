@@ -84,7 +84,7 @@ void free_plan(Plan& p) {
     void* ptrs[] = {p.pos,   p.tile_ptr,   p.tile_frames, p.w_cur, p.w_form,     p.w2,
                     p.Dsum,  p.invD,       p.dmax_bits,   p.accA,  p.accB,       p.ebuf,
                     p.sums,  p.probe_part, p.probe_acc,   p.scal,  p.w2tmp,      p.Dtmp,
-                    p.invDtmp, p.errflag};
+                    p.invDtmp, p.errflag, p.counter};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     std::memset(&p, 0, sizeof(p));
@@ -102,6 +102,7 @@ sharp::FrameArgs base_args(const Plan& p) {
     a.beta = p.prm.beta;
     a.sums = p.sums;
     a.err = p.errflag;
+    a.counter = p.counter;
     return a;
 }
 
@@ -211,6 +212,7 @@ int sharp_plan_create(sharp_plan* out, int K, int m, int ny, int nx, const int32
     SHARP_ALLOC(Dtmp, n)
     SHARP_ALLOC(invDtmp, n)
     SHARP_ALLOC(errflag, 1)
+    SHARP_ALLOC(counter, 1)
 #undef SHARP_ALLOC
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.pos, hpos.data(), hpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.tile_ptr, count.data(), count.size() * sizeof(int), cudaMemcpyHostToDevice, stream);

@@ -109,6 +109,7 @@ struct Plan {
     bool form_differs;       // w_form != w_cur (a probe update happened)
     void* prof;              // kernel-timing state (sharp_api.cu), nullptr when off
     int* errflag;            // device int: sticky error raised inside kernels
+    int* counter;            // device int: work counter of the persistent frame pass
 };
 
 constexpr int TILE = 32;
@@ -143,6 +144,7 @@ struct FrameArgs {
     float gscale;
     double* sums;            // per-mode accumulators
     int* err;                // device error flag (SHARP_ERR_TIMEOUT on a bounded-wait failure)
+    int* counter;            // frame counter of the persistent RAAR pass (zeroed per launch)
 };
 
 // compile-time flags of MODE_RAAR
