@@ -192,6 +192,28 @@ int sharp_amp_loss_backward(sharp_plan plan, const float2* obj, const float2* pr
                             float2* g_probe, cudaStream_t stream);
 
 /*
+ * Data projection without device allocation.  The paper has no counterpart:
+ * this entry point serves callers that must not allocate device memory while
+ * they run -- hosts that own every device allocation, real-time loops that
+ * cannot risk the synchronisation an allocation may cause, or work recorded
+ * into a CUDA graph.  It needs no plan.
+ *   z, out   : float2[K][m][m] (out == z allowed);  amp : float[K][m][m];
+ *   resid_sq : DEVICE double[1] or NULL; receives ||P_a z - z||^2, summed over
+ *              frames in frame order.
+ *   Same result as sharp_fourier_project (Eq. 7, phase 1 where F z = 0).
+ * Its only scratch, one residual per frame, lives in a fixed library-owned
+ * device array of SHARP_NOALLOC_MAX_FRAMES doubles (512 KiB) that every GPU
+ * using the library keeps until the process exits; K above that limit
+ * returns SHARP_ERR_INVALID_ARG.  The first call on each device looks up the
+ * array's device address (make it before any stream capture).  All calls
+ * share the array: calls that overlap on the GPU race, so serialise them.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE (m not 64 or 128), CUDA.
+ */
+#define SHARP_NOALLOC_MAX_FRAMES 65536
+int sharp_fourier_project_noalloc(const float2* z, const float* amp, float2* out, double* resid_sq,
+                                  int K, int m, cudaStream_t stream);
+
+/*
  * Synchronise `stream` and report a sticky device-side failure of the plan's
  * kernels: SHARP_ERR_TIMEOUT when a bounded wait for a bulk copy gave up
  * (the affected step's results are invalid).  Clears the flag.

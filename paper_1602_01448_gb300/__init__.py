@@ -20,7 +20,7 @@ __all__ = [
     "sharp_overlap_project", "sharp_probe_update", "sharp_raar_init", "sharp_raar_step",
     "sharp_solution_error", "sharp_forward_amplitudes", "sharp_amp_loss",
     "sharp_amp_loss_backward", "AmpLoss", "amp_loss", "sharp_plan_set_profiling",
-    "sharp_plan_kernel_times", "sharp_plan_status",
+    "sharp_plan_kernel_times", "sharp_plan_status", "sharp_fourier_project_noalloc",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -76,6 +76,7 @@ _lib_fns = {
     "sharp_amp_loss_backward": ([_P, _P, _P, _P, _D, _P, _P, _P], _I),
     "sharp_plan_set_profiling": ([_P, _I], _I),
     "sharp_plan_status": ([_P, _P], _I),
+    "sharp_fourier_project_noalloc": ([_P, _P, _P, _P, _I, _I, _P], _I),
     "sharp_plan_kernel_times": ([_P, _P, _P], _I),
 }
 _C = {name: _decl(name, *sig) for name, sig in _lib_fns.items()}
@@ -191,6 +192,13 @@ def sharp_amp_loss_backward(plan, obj, probe, amp, grad_scale, g_obj, g_probe=No
 
 
 KCLASSES = ("frame", "image", "probe", "illum", "other")
+
+
+def sharp_fourier_project_noalloc(z, amp, out, resid_sq=None, stream=None) -> None:
+    """P_a of explicit frames without any device allocation (no plan)."""
+    K, m = int(z.shape[0]), int(z.shape[-1])
+    _check(_C["sharp_fourier_project_noalloc"](_c64(z, "z"), _f32(amp, "amp"), _c64(out, "out"),
+                                               _f64(resid_sq, "resid_sq"), K, m, _stream(stream)))
 
 
 def sharp_plan_status(plan, stream=None) -> None:

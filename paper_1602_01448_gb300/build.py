@@ -19,7 +19,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libsharp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["raar_128_w0.cu", "raar_128_w1.cu", "raar_64_w0.cu", "raar_64_w1.cu", "frame_kernels_128.cu",
-           "frame_kernels_64.cu", "image_kernels.cu", "sharp_api.cu"]
+           "frame_kernels_64.cu", "image_kernels.cu", "sharp_api.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -60,13 +60,14 @@ __global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 
     for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
-        const int py = a.pos[2 * i];
-        const int px = a.pos[2 * i + 1];
+        // explicit frames carry no position (the plan-free projection has none)
+        const int py = (MODE == MODE_PROJECT_PF) ? 0 : a.pos[2 * i];
+        const int px = (MODE == MODE_PROJECT_PF) ? 0 : a.pos[2 * i + 1];
         const size_t fo = (size_t)i * MM;
         float2 v[32];
 
         // ------------------------------------------------ form the frame
-        if constexpr (MODE == MODE_PROJECT) {
+        if constexpr (MODE == MODE_PROJECT || MODE == MODE_PROJECT_PF) {
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
                 const int y = q + TX * k;
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a
                     const float av = __ldg(ai + ky * M + kx);
                     const float d = av - mag;
                     acc[0] += d * d;
-                    if constexpr (MODE == MODE_PROJECT) {
+                    if constexpr (MODE == MODE_PROJECT || MODE == MODE_PROJECT_PF) {
                         // Z'' = (a Z/|Z|) / m so that the raw inverse gives P_a z
                         X = m2 > 0.f ? cscale(X, av * inv_m * rs) : make_float2(av * inv_m, 0.f);
                     } else if constexpr (MODE == MODE_GRAD) {
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a
         G::inverse(v, S, tw);
 
         // ------------------------------------------------ epilogue
-        if constexpr (MODE == MODE_PROJECT) {
+        if constexpr (MODE == MODE_PROJECT || MODE == MODE_PROJECT_PF) {
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
                 const int y = q + TX * k;
@@ -138,11 +139,20 @@ __global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a
                 if ((k % CHUNK) == CHUNK - 1) chunk_fence();
             }
         }
+        if constexpr (MODE == MODE_PROJECT_PF) {
+            // one residual per frame, each written by its own block
+            block_sum<NT, 5>(acc, red);
+            if (tid == 0) a.sums[i] = (double)acc[0];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) acc[j] = 0.f;
+        }
     }
 
-    block_sum<NT, 5>(acc, red);
-    if (tid == 0) {
-        if constexpr (MODE != MODE_AMPS) atomicAdd(a.sums, (double)acc[0]);
+    if constexpr (MODE != MODE_PROJECT_PF) {
+        block_sum<NT, 5>(acc, red);
+        if (tid == 0) {
+            if constexpr (MODE != MODE_AMPS) atomicAdd(a.sums, (double)acc[0]);
+        }
     }
 }
 

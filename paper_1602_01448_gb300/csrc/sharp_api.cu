@@ -113,6 +113,8 @@ int check_plan(sharp_plan plan) {
 
 }  // namespace
 
+void sharp::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 extern "C" {
 
 const char* sharp_last_error(void) { return g_err.c_str(); }

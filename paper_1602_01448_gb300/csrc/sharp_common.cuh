@@ -115,7 +115,8 @@ struct Plan {
 constexpr int TILE = 32;
 
 // ------------------------------------------------ launchers (frame_kernels.cu)
-enum FrameMode { MODE_RAAR = 0, MODE_PROJECT = 1, MODE_AMPS = 2, MODE_LOSS = 3, MODE_GRAD = 4 };
+enum FrameMode { MODE_RAAR = 0, MODE_PROJECT = 1, MODE_AMPS = 2, MODE_LOSS = 3, MODE_GRAD = 4,
+                 MODE_PROJECT_PF = 5 /* P_a with one residual per frame in sums[i] */ };
 
 struct FrameArgs {
     int K, m, ny, nx, wrap;
@@ -186,6 +187,9 @@ cudaError_t launch_metrics_finalize(const Plan& p, double* metrics, int have_q, 
 cudaError_t launch_solution_error(Plan& p, const float2* psi, const float2* psi_true, const float2* probe,
                                   double* out, cudaStream_t s);
 cudaError_t launch_copy_scaled(const double* src, double* dst, double scale, cudaStream_t s);
+
+// Message returned by sharp_last_error() on this thread (sharp_api.cu).
+void set_last_error(const char* msg);
 
 // slots of Plan::sums
 enum SumSlot {
