@@ -47,14 +47,17 @@ illum_gather_kernel(const int32_t* __restrict__ pos, const int* __restrict__ tpt
     const int gx = (tile % tiles_x) * TILE + (threadIdx.x & 31);
     const int gy0 = (tile / tiles_x) * TILE + (threadIdx.x >> 5);
     float s[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int j = tptr[tile]; j < tptr[tile + 1]; ++j) {
-        const int f = tfr[j];
-        const int py = pos[2 * f], px = pos[2 * f + 1];
-        const int lx = local_offset(gx, px, nx, wrap, m);
+    const int j0 = tptr[tile], j1 = tptr[tile + 1];
+    for (int j = j0; j < j1; ++j) {
+        const int f = __ldg(tfr + j);
+        const int lx = local_offset(gx, __ldg(pos + 2 * f + 1), nx, wrap, m);
+        if (lx >= m) continue;                 // this column is outside frame f
+        const int py = __ldg(pos + 2 * f);
+        const float* wr = w2 + lx;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int ly = local_offset(gy0 + 8 * r, py, ny, wrap, m);
-            if (lx < m && ly < m) kahan_add(s[r], cc[r], __ldg(w2 + ly * m + lx));
+            if (ly < m) kahan_add(s[r], cc[r], __ldg(wr + ly * m));
         }
     }
     float mx = 0.f;
@@ -170,6 +173,7 @@ __global__ void probe_partial_kernel(const int32_t* __restrict__ pos, const floa
                                      const float2* __restrict__ zc, const float2* __restrict__ psiy,
                                      const float2* __restrict__ w, float* __restrict__ part, int K, int m,
                                      int ny, int nx, int wrap) {
+    constexpr int U = 4;   // frames in flight per thread
     const int mm = m * m;
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= mm) return;
@@ -179,15 +183,25 @@ __global__ void probe_partial_kernel(const int32_t* __restrict__ pos, const floa
     const int f1 = min(K, f0 + PROBE_CHUNK);
     const float2 wl = psiy ? __ldg(w + l) : make_float2(0.f, 0.f);
     float nr = 0.f, ni = 0.f, dn = 0.f;
-    for (int f = f0; f < f1; ++f) {
-        const int o = obj_index(pos[2 * f], pos[2 * f + 1], y, x, ny, nx, wrap);
-        const float2 ps = __ldg(psi + o);
-        float2 z = __ldg(zc + (size_t)f * mm + l);
-        if (psiy) z = cadd(z, cmul(wl, __ldg(psiy + o)));
-        const float2 t = cmulc(ps, z);
-        nr += t.x;
-        ni += t.y;
-        dn += cabs2(ps);
+    for (int f = f0; f < f1; f += U) {
+        float2 ps[U], zz[U], yy[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int g = min(f + u, f1 - 1);
+            const int o = obj_index(pos[2 * g], pos[2 * g + 1], y, x, ny, nx, wrap);
+            ps[u] = __ldg(psi + o);
+            zz[u] = __ldcs(zc + (size_t)g * mm + l);
+            yy[u] = psiy ? __ldg(psiy + o) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (f + u >= f1) break;
+            const float2 z = psiy ? cadd(zz[u], cmul(wl, yy[u])) : zz[u];
+            const float2 t = cmulc(ps[u], z);
+            nr += t.x;
+            ni += t.y;
+            dn += cabs2(ps[u]);
+        }
     }
     float* pc = part + (size_t)chunk * 3 * mm;
     pc[l] = nr;

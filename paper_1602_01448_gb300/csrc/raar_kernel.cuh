@@ -167,23 +167,29 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
         // Y = ((1-2b) a Z/|Z| + b Z) / m on the unitary scale, so the raw
         // inverse returns c_new directly; phase 1 where Z = 0.
         const float* ai = a.amp + fo;
+        // amplitudes in batches of CH loads in flight, then the arithmetic
 #pragma unroll
-        for (int c = 0; c < G::C3; ++c) {
-            const int ky = G::p3_ky(c);
+        for (int j0 = 0; j0 < 32; j0 += CH) {
+            float av[CH];
 #pragma unroll
-            for (int s = 0; s < G::X0; ++s) {
-                const int kx = G::p3_kx(s);
-                float2& X = v[c * G::X0 + s];
-                const float av = __ldcs(ai + ky * M + kx);   // streamed once: evict-first
+            for (int j = j0; j < j0 + CH; ++j) {
+                const int c = j / G::X0, s = j % G::X0;
+                av[j - j0] = __ldcs(ai + G::p3_ky(c) * M + G::p3_kx(s));   // streamed once
+            }
+#pragma unroll
+            for (int j = j0; j < j0 + CH; ++j) {
+                float2& X = v[j];
                 const float m2 = cabs2(X);
                 const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
-                const float d = av - m2 * rs * inv_m;
+                const float d = av[j - j0] - m2 * rs * inv_m;
                 acc[0] += d * d;
-                acc[1] += av * av;
-                X = m2 > 0.f ? cscale(X, fmaf(cp * av, rs, b * inv_m) * inv_m)
-                             : make_float2(cp * av * inv_m, 0.f);
+                acc[1] += av[j - j0] * av[j - j0];
+                X = m2 > 0.f ? cscale(X, fmaf(cp * av[j - j0], rs, b * inv_m) * inv_m)
+                             : make_float2(cp * av[j - j0] * inv_m, 0.f);
             }
+            chunk_fence_r();
         }
+
         G::inverse(v, S, tw);
 
         fence_proxy_async_smem();
