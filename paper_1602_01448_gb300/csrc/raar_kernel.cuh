@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
     constexpr int NT = G::NT;
     constexpr int TX = G::TX;
     constexpr int MM = M * M;
-    constexpr int CH = 8;
+    constexpr int CH = 16;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2* S = reinterpret_cast<float2*>(smem_raw);
     float2* tw = reinterpret_cast<float2*>(smem_raw + R::S_BYTES);
@@ -167,27 +167,22 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
         // Y = ((1-2b) a Z/|Z| + b Z) / m on the unitary scale, so the raw
         // inverse returns c_new directly; phase 1 where Z = 0.
         const float* ai = a.amp + fo;
-        // amplitudes in batches of CH loads in flight, then the arithmetic
+        {
+            // all 32 amplitude loads in flight at once, then the arithmetic
+            float av[32];
 #pragma unroll
-        for (int j0 = 0; j0 < 32; j0 += CH) {
-            float av[CH];
+            for (int j = 0; j < 32; ++j) av[j] = __ldcs(ai + G::p3_ky(j / G::X0) * M + G::p3_kx(j % G::X0));
 #pragma unroll
-            for (int j = j0; j < j0 + CH; ++j) {
-                const int c = j / G::X0, s = j % G::X0;
-                av[j - j0] = __ldcs(ai + G::p3_ky(c) * M + G::p3_kx(s));   // streamed once
-            }
-#pragma unroll
-            for (int j = j0; j < j0 + CH; ++j) {
+            for (int j = 0; j < 32; ++j) {
                 float2& X = v[j];
                 const float m2 = cabs2(X);
                 const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
-                const float d = av[j - j0] - m2 * rs * inv_m;
+                const float d = av[j] - m2 * rs * inv_m;
                 acc[0] += d * d;
-                acc[1] += av[j - j0] * av[j - j0];
-                X = m2 > 0.f ? cscale(X, fmaf(cp * av[j - j0], rs, b * inv_m) * inv_m)
-                             : make_float2(cp * av[j - j0] * inv_m, 0.f);
+                acc[1] += av[j] * av[j];
+                X = m2 > 0.f ? cscale(X, fmaf(cp * av[j], rs, b * inv_m) * inv_m)
+                             : make_float2(cp * av[j] * inv_m, 0.f);
             }
-            chunk_fence_r();
         }
 
         G::inverse(v, S, tw);
