@@ -119,6 +119,23 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+def slowest_rank_ms(ms: float, world: int, device=None) -> float:
+    """Max over ranks of a per-rank time (the job is as slow as its slowest
+    replica); identity for a single process."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(frames_per_rank: int, steps: int, world: int, ms_total: float) -> float:
+    """Whole-job frame-iterations per second: every rank runs its own replica
+    of the scan (weak scaling), timed by the slowest rank."""
+    return world * frames_per_rank * steps / (ms_total / 1000.0)
+
+
 def make_scan(frames: int = 2500):
     import synth
     return synth.scan_fermat(count=frames)
@@ -226,12 +243,9 @@ def run_ours(args, rank, world):
     kt = S.sharp_plan_kernel_times(plan.handle)
     S.sharp_plan_set_profiling(plan.handle, False)
     metrics = plan.metrics.cpu().numpy().tolist()
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = slowest_rank_ms(ms_total, world, dev)
     ms_step = ms_total / args.steps
-    value = world * K * args.steps / (ms_total / 1000.0)
+    value = job_throughput(K, args.steps, world, ms_total)
 
     # roofline of the fused frame kernel: 20 m^2 B per frame-iteration
     frame_ms, frame_n = kt["frame"]
@@ -259,10 +273,7 @@ def run_ours(args, rank, world):
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = slowest_rank_ms(e2e_ms, world, dev)
 
     if rank != 0:
         return

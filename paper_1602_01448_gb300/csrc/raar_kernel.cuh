@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
     constexpr int NT = G::NT;
     constexpr int TX = G::TX;
     constexpr int MM = M * M;
-    constexpr int CH = 16;
+    constexpr int CH = 8;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2* S = reinterpret_cast<float2*>(smem_raw);
     float2* tw = reinterpret_cast<float2*>(smem_raw + R::S_BYTES);

@@ -10,8 +10,11 @@
 namespace sharp {
 
 // ---------------------------------------------------------------- complex
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add / subtract on the packed FP32x2 pipe of sm_100-class GPUs: one
+// instruction per complex operation (a float2 already occupies an aligned
+// register pair).  b * (-1) + a rounds exactly like a - b.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // a * b
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
