@@ -297,7 +297,7 @@ def run_ours(args, rank, world):
                    "l2": "inputs larger than L2 (c 328 MB + a 164 MB per step)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(),
-                     "kernel": "frame_kernel<128,RAAR>", "peak_kind": peak_kind,
+                     "kernel": "raar_kernel<128>", "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes, "kernel_ms": t_frame * 1000.0},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "cpu_baseline": cpu,

@@ -192,6 +192,39 @@ int sharp_amp_loss_backward(sharp_plan plan, const float2* obj, const float2* pr
                             float2* g_probe, cudaStream_t stream);
 
 /*
+ * Batched RAAR: independent scans (the multi-scan workloads of a streaming
+ * beamline, Sec. 3) stepped together.  Each scan keeps its own plan, state,
+ * amplitudes and probe; every sharp_batch_step(iter) performs one RAAR step
+ * (as sharp_raar_step) for every scan with one persistent frame-pass launch
+ * per frame size over the frames of all scans of that size, then each scan's
+ * image pass, metrics and probe update.  The launch sequence of each distinct
+ * step schedule is recorded as a CUDA graph on first use and replayed
+ * afterwards; while the grid autotuner is still trying blocks-per-SM
+ * candidates (the first steps of a frame size with several), steps run
+ * without graphs and synchronise the stream.  Results do not depend on the
+ * grid or on graphs.
+ *   plans : nscans plans, already set up with sharp_raar_init; they must share
+ *           probe_every and residual_every and be stepped only through the
+ *           batch.  The batch does not own them.
+ * sharp_batch_bind gives scan `scan` its state buffers (as sharp_raar_step;
+ * probe and metrics may be NULL); rebinding drops the recorded graphs.
+ * sharp_batch_tuned_grid returns the grid chosen for frame size m (or -1).
+ * sharp_batch_status synchronises `stream` and returns SHARP_ERR_TIMEOUT
+ * (once) if a bounded wait of a batched frame pass gave up; the affected
+ * scan's plan reports it through sharp_plan_status as well.
+ * Errors: INVALID_ARG, STATE (unbound scan, diverging schedules), CUDA.
+ */
+typedef struct sharp_batch_s* sharp_batch;
+int sharp_batch_create(sharp_batch* batch, int nscans, const sharp_plan* plans);
+int sharp_batch_bind(sharp_batch batch, int scan, float2* state_c, float2* psi_y, float2* psi, float2* probe,
+                     const float* amp, double* metrics);
+int sharp_batch_step(sharp_batch batch, int iter, cudaStream_t stream);
+int sharp_batch_set_graphs(sharp_batch batch, int enable);
+int sharp_batch_tuned_grid(sharp_batch batch, int m);
+int sharp_batch_status(sharp_batch batch, cudaStream_t stream);
+int sharp_batch_destroy(sharp_batch batch);
+
+/*
  * Data projection without device allocation.  The paper has no counterpart:
  * this entry point serves callers that must not allocate device memory while
  * they run -- hosts that own every device allocation, real-time loops that

@@ -20,7 +20,7 @@ __all__ = [
     "sharp_overlap_project", "sharp_probe_update", "sharp_raar_init", "sharp_raar_step",
     "sharp_solution_error", "sharp_forward_amplitudes", "sharp_amp_loss",
     "sharp_amp_loss_backward", "AmpLoss", "amp_loss", "sharp_plan_set_profiling",
-    "sharp_plan_kernel_times", "sharp_plan_status", "sharp_fourier_project_noalloc",
+    "sharp_plan_kernel_times", "sharp_plan_status", "sharp_fourier_project_noalloc", "Batch",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -77,6 +77,13 @@ _lib_fns = {
     "sharp_plan_set_profiling": ([_P, _I], _I),
     "sharp_plan_status": ([_P, _P], _I),
     "sharp_fourier_project_noalloc": ([_P, _P, _P, _P, _I, _I, _P], _I),
+    "sharp_batch_create": ([ctypes.POINTER(_P), _I, ctypes.POINTER(_P)], _I),
+    "sharp_batch_bind": ([_P, _I, _P, _P, _P, _P, _P, _P], _I),
+    "sharp_batch_step": ([_P, _I, _P], _I),
+    "sharp_batch_set_graphs": ([_P, _I], _I),
+    "sharp_batch_tuned_grid": ([_P, _I], _I),
+    "sharp_batch_status": ([_P, _P], _I),
+    "sharp_batch_destroy": ([_P], _I),
     "sharp_plan_kernel_times": ([_P, _P, _P], _I),
 }
 _C = {name: _decl(name, *sig) for name, sig in _lib_fns.items()}
@@ -251,6 +258,10 @@ class Plan:
         except Exception:
             pass
 
+    def status(self, stream=None):
+        """Raise SharpError if a bounded device-side wait of this plan gave up."""
+        _check(_C["sharp_plan_status"](self.handle, _stream(stream)))
+
     # ---------------------------------------------------------- operators
     def q_gather(self, obj, probe):
         out = torch.empty((self.K, self.m, self.m), dtype=torch.complex64, device=self.device)
@@ -299,6 +310,53 @@ class Plan:
         sharp_raar_step(self.handle, self.c, self.psi_y, self.psi, self.probe, amp,
                         self.metrics if metrics else None, self.iter)
         return self.metrics if metrics else None
+
+
+class Batch:
+    """Independent scans stepped together by ``sharp_batch_step``: one
+    persistent frame-pass launch per frame size, each step schedule recorded
+    as a CUDA graph.  ``plans`` are ``Plan`` objects after ``raar_init``,
+    ``amps`` their measured amplitudes; ``metrics`` of each plan are filled as
+    by ``Plan.raar_step``."""
+
+    def __init__(self, plans, amps, use_graphs=True):
+        self.plans = list(plans)
+        self.amps = list(amps)
+        if len(self.amps) != len(self.plans):
+            raise ValueError("one amplitude tensor per plan")
+        arr = (_P * len(self.plans))(*[p.handle for p in self.plans])
+        h = _P()
+        _check(_C["sharp_batch_create"](ctypes.byref(h), len(self.plans), arr))
+        self.handle = h.value
+        _check(_C["sharp_batch_set_graphs"](self.handle, int(bool(use_graphs))))
+        for i, (p, a) in enumerate(zip(self.plans, self.amps)):
+            _check(_C["sharp_batch_bind"](self.handle, i, _c64(p.c, "state_c"), _c64(p.psi_y, "psi_y"),
+                                          _c64(p.psi, "psi"), _c64(p.probe, "probe"),
+                                          _f32(a, "amp", (p.K, p.m, p.m)), _f64(p.metrics, "metrics")))
+        self.iter = 0
+
+    def step(self, stream=None):
+        self.iter += 1
+        for p in self.plans:
+            p.iter = self.iter
+        _check(_C["sharp_batch_step"](self.handle, self.iter, _stream(stream)))
+
+    def tuned_grid(self, m):
+        return int(_C["sharp_batch_tuned_grid"](self.handle, int(m)))
+
+    def status(self, stream=None):
+        _check(_C["sharp_batch_status"](self.handle, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(_C["sharp_batch_destroy"](self.handle))
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class AmpLoss(torch.autograd.Function):

@@ -39,25 +39,38 @@ __global__ void w2_kernel(const float2* __restrict__ w, float* __restrict__ w2, 
         w2[i] = cabs2(w[i]);
 }
 
+// Frame list entries of a tile staged in shared memory per round.
+constexpr int GATHER_STAGE = 512;
+
 __global__ void __launch_bounds__(GATHER_THREADS)
 illum_gather_kernel(const int32_t* __restrict__ pos, const int* __restrict__ tptr,
                     const int* __restrict__ tfr, const float* __restrict__ w2, float* __restrict__ D,
                     unsigned* __restrict__ dmax_bits, int m, int ny, int nx, int tiles_x, int wrap) {
+    __shared__ int2 sp[GATHER_STAGE];          // (row, col) of the staged frames
     const int tile = blockIdx.x;
     const int gx = (tile % tiles_x) * TILE + (threadIdx.x & 31);
     const int gy0 = (tile / tiles_x) * TILE + (threadIdx.x >> 5);
     float s[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
     const int j0 = tptr[tile], j1 = tptr[tile + 1];
-    for (int j = j0; j < j1; ++j) {
-        const int f = __ldg(tfr + j);
-        const int lx = local_offset(gx, __ldg(pos + 2 * f + 1), nx, wrap, m);
-        if (lx >= m) continue;                 // this column is outside frame f
-        const int py = __ldg(pos + 2 * f);
-        const float* wr = w2 + lx;
+    for (int base = j0; base < j1; base += GATHER_STAGE) {
+        const int n = min(GATHER_STAGE, j1 - base);
+        __syncthreads();
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            const int f = __ldg(tfr + base + t);
+            sp[t] = make_int2(__ldg(pos + 2 * f), __ldg(pos + 2 * f + 1));
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int t = 0; t < n; ++t) {
+            const int2 p = sp[t];
+            const int lx = local_offset(gx, p.y, nx, wrap, m);
+            if (lx >= m) continue;             // this column is outside the frame
+            const float* wr = w2 + lx;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int ly = local_offset(gy0 + 8 * r, py, ny, wrap, m);
-            if (ly < m) kahan_add(s[r], cc[r], __ldg(wr + ly * m));
+            for (int r = 0; r < 4; ++r) {
+                const int ly = local_offset(gy0 + 8 * r, p.x, ny, wrap, m);
+                if (ly < m) kahan_add(s[r], cc[r], __ldg(wr + ly * m));
+            }
         }
     }
     float mx = 0.f;
@@ -419,11 +432,11 @@ static cudaError_t probe_common(Plan& p, const float2* psi, const float2* zc, co
 
 cudaError_t launch_probe_update_state(Plan& p, const float2* c, const float2* psiy, const float2* psi,
                                       cudaStream_t s) {
-    // z^(l) = w_cur . psi_y + c; the refined probe replaces w_cur, and the old
-    // one becomes w_form (it formed the iterate).
-    float2* old = p.w_cur;
-    p.w_cur = p.w_form;
-    p.w_form = old;
+    // z^(l) = w_cur . psi_y + c.  The current probe is copied to w_form (it
+    // formed the iterate) and the refined probe is written to w_cur; the
+    // buffers keep their addresses, so recorded CUDA graphs stay valid.
+    cudaError_t e = cudaMemcpyAsync(p.w_form, p.w_cur, sizeof(float2) * p.m * p.m, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
     return probe_common(p, psi, c, psiy, p.w_form, p.w_form, p.w_cur, s);
 }
 

@@ -44,29 +44,139 @@ __device__ __forceinline__ void chunk_fence_r() { asm volatile("" ::: "memory");
 template <class T>
 __device__ __forceinline__ T ldg_plain(const T* p) { return *p; }
 
+// ------------------------------------------------------------------ phases
+// The three per-frame phases, shared by the single-scan and the batch kernel.
+// `a` is the scan's arguments (kernel parameter or a shared-memory copy).
+
+// z = w_f . psi_y(r + x_i) + c_i into v (pass-1 layout); c_i is in S.
 template <int M, int FLAGS, int WRAP>
-__global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(const FrameArgs a) {
+__device__ __forceinline__ void raar_load_phase(const FrameArgs& a, int py, int px, size_t fo, const float2* S,
+                                                float2 (&v)[32], float (&acc)[5], uint64_t pol_stream,
+                                                uint64_t pol_keep) {
+    constexpr int TX = Fft3<M>::TX;
+    constexpr int CH = 8;
+    const int q = threadIdx.x / M;
+    const int x = threadIdx.x % M;
+    // Per chunk of CH rows: issue every load first, then compute, then store
+    // (a store ahead of the next row's loads would serialise them).
+#pragma unroll
+    for (int k0 = 0; k0 < 32; k0 += CH) {
+        float2 wf[CH], yv[CH], pv[CH], ev[CH];
+#pragma unroll
+        for (int k = k0; k < k0 + CH; ++k) {
+            const int y = q + TX * k;
+            const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
+            wf[k - k0] = ld_hint(a.w_form + y * M + x, pol_keep);
+            yv[k - k0] = ld_hint(a.psiy + o, pol_keep);
+            if constexpr (FLAGS & RF_METRIC) {
+                pv[k - k0] = ld_hint(a.psi + o, pol_keep);
+                ev[k - k0] = a.read_e ? ld_hint(a.ebuf + fo + y * M + x, pol_stream) : make_float2(0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int k = k0; k < k0 + CH; ++k) {
+            const int y = q + TX * k;
+            const float2 wy = cmul(wf[k - k0], yv[k - k0]);
+            const float2 z = cadd(wy, S[y * M + x]);
+            v[k] = z;
+            acc[2] += cabs2(z);
+            if constexpr (FLAGS & RF_METRIC) {
+                acc[3] += cabs2(csub(cmul(wf[k - k0], pv[k - k0]), z));
+                acc[4] += cabs2(cadd(wy, ev[k - k0]));
+            }
+        }
+        if constexpr (FLAGS & RF_FORM_B) {
+#pragma unroll
+            for (int k = k0; k < k0 + CH; ++k) {
+                const int y = q + TX * k;
+                const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
+                red_hint(a.accB + o, cmulc(ld_hint(a.w_proj + y * M + x, pol_keep), v[k]), pol_keep);
+            }
+        }
+        if (a.write_e) {
+#pragma unroll
+            for (int k = k0; k < k0 + CH; ++k) {
+                const int y = q + TX * k;
+                st_hint(a.ebuf + fo + y * M + x, make_float2(-v[k].x, -v[k].y), pol_stream);
+            }
+        }
+        chunk_fence_r();
+    }
+}
+
+// Y = ((1-2b) a Z/|Z| + b Z) / m on the unitary scale (pass-3 layout), so the
+// raw inverse returns c_new directly; phase 1 where Z = 0.
+template <int M>
+__device__ __forceinline__ void raar_fourier_phase(const FrameArgs& a, size_t fo, float2 (&v)[32],
+                                                   float (&acc)[5]) {
+    using G = Fft3<M>;
+    const float inv_m = 1.0f / M;
+    const float b = a.beta;
+    const float cp = 1.f - 2.f * b;
+    const float* ai = a.amp + fo;
+    // all 32 amplitude loads in flight at once, then the arithmetic
+    float av[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) av[j] = __ldcs(ai + G::p3_ky(j / G::X0) * M + G::p3_kx(j % G::X0));
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        float2& X = v[j];
+        const float m2 = cabs2(X);
+        const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
+        const float d = av[j] - m2 * rs * inv_m;
+        acc[0] += d * d;
+        acc[1] += av[j] * av[j];
+        X = m2 > 0.f ? cscale(X, fmaf(cp * av[j], rs, b * inv_m) * inv_m)
+                     : make_float2(cp * av[j] * inv_m, 0.f);
+    }
+}
+
+// Store c_new and scatter C += conj(w_p) c_new (pass-1 layout).
+template <int M, int WRAP>
+__device__ __forceinline__ void raar_epilogue(const FrameArgs& a, int py, int px, size_t fo, const float2 (&v)[32],
+                                              uint64_t pol_stream, uint64_t pol_keep) {
+    constexpr int TX = Fft3<M>::TX;
+    constexpr int CH = 8;
+    const int q = threadIdx.x / M;
+    const int x = threadIdx.x % M;
+#pragma unroll
+    for (int k0 = 0; k0 < 32; k0 += CH) {
+        float2 wp[CH];
+#pragma unroll
+        for (int k = k0; k < k0 + CH; ++k) wp[k - k0] = ld_hint(a.w_proj + (q + TX * k) * M + x, pol_keep);
+#pragma unroll
+        for (int k = k0; k < k0 + CH; ++k) {
+            const int y = q + TX * k;
+            const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
+            const float2 cn = v[k];
+            st_hint(a.c + fo + y * M + x, cn, pol_stream);
+            red_hint(a.accA + o, cmulc(wp[k - k0], cn), pol_keep);
+            if (a.write_e) red_hint(a.ebuf + fo + y * M + x, cn, pol_stream);
+        }
+        chunk_fence_r();
+    }
+}
+
+// ------------------------------------------------------------------ single scan
+template <int M, int FLAGS, int WRAP>
+__global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(const FrameArgs ap) {
     using G = Fft3<M>;
     using R = RaarGeo<M>;
     constexpr int NT = G::NT;
-    constexpr int TX = G::TX;
     constexpr int MM = M * M;
-    constexpr int CH = 8;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2* S = reinterpret_cast<float2*>(smem_raw);
     float2* tw = reinterpret_cast<float2*>(smem_raw + R::S_BYTES);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + R::S_BYTES + R::TW_BYTES);
     __shared__ float red[32 * 5];
-
+    // Arguments served from shared memory: the compiler re-reads them where
+    // needed instead of holding pointers in registers (it spills much less).
+    __shared__ FrameArgs a;
     const int tid = threadIdx.x;
-    const int q = tid / M;
-    const int x = tid % M;
-    const float inv_m = 1.0f / M;
-    const float b = a.beta;
-    const float cp = 1.f - 2.f * b;
 
     G::load_twiddles(tw);
     if (tid == 0) {
+        a = ap;
         mbar_init(&bars[0], 1);
         mbar_fence_init();
     }
@@ -114,77 +224,9 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
         c_pending = false;
         const int nxt = s_next;   // published before the barrier above
 
-        // ---------------------------------------------- z = w_f . psi_y + c
-        // Per chunk of CH rows: issue every load first, then compute, then
-        // store (a store ahead of the next row's loads would serialise them).
-#pragma unroll
-        for (int k0 = 0; k0 < 32; k0 += CH) {
-            float2 wf[CH], yv[CH], pv[CH], ev[CH];
-#pragma unroll
-            for (int k = k0; k < k0 + CH; ++k) {
-                const int y = q + TX * k;
-                const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
-                wf[k - k0] = ld_hint(a.w_form + y * M + x, pol_keep);
-                yv[k - k0] = ld_hint(a.psiy + o, pol_keep);
-                if constexpr (FLAGS & RF_METRIC) {
-                    pv[k - k0] = ld_hint(a.psi + o, pol_keep);
-                    ev[k - k0] = a.read_e ? ld_hint(a.ebuf + fo + y * M + x, pol_stream) : make_float2(0.f, 0.f);
-                }
-            }
-#pragma unroll
-            for (int k = k0; k < k0 + CH; ++k) {
-                const int y = q + TX * k;
-                const float2 wy = cmul(wf[k - k0], yv[k - k0]);
-                const float2 z = cadd(wy, S[y * M + x]);
-                v[k] = z;
-                acc[2] += cabs2(z);
-                if constexpr (FLAGS & RF_METRIC) {
-                    acc[3] += cabs2(csub(cmul(wf[k - k0], pv[k - k0]), z));
-                    acc[4] += cabs2(cadd(wy, ev[k - k0]));
-                }
-            }
-            if constexpr (FLAGS & RF_FORM_B) {
-#pragma unroll
-                for (int k = k0; k < k0 + CH; ++k) {
-                    const int y = q + TX * k;
-                    const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
-                    red_hint(a.accB + o, cmulc(ld_hint(a.w_proj + y * M + x, pol_keep), v[k]), pol_keep);
-                }
-            }
-            if (a.write_e) {
-#pragma unroll
-                for (int k = k0; k < k0 + CH; ++k) {
-                    const int y = q + TX * k;
-                    st_hint(a.ebuf + fo + y * M + x, make_float2(-v[k].x, -v[k].y), pol_stream);
-                }
-            }
-            chunk_fence_r();
-        }
-
+        raar_load_phase<M, FLAGS, WRAP>(a, py, px, fo, S, v, acc, pol_stream, pol_keep);
         G::forward(v, S, tw);
-
-        // ---------------------------------------------- Fourier domain
-        // Y = ((1-2b) a Z/|Z| + b Z) / m on the unitary scale, so the raw
-        // inverse returns c_new directly; phase 1 where Z = 0.
-        const float* ai = a.amp + fo;
-        {
-            // all 32 amplitude loads in flight at once, then the arithmetic
-            float av[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) av[j] = __ldcs(ai + G::p3_ky(j / G::X0) * M + G::p3_kx(j % G::X0));
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                float2& X = v[j];
-                const float m2 = cabs2(X);
-                const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
-                const float d = av[j] - m2 * rs * inv_m;
-                acc[0] += d * d;
-                acc[1] += av[j] * av[j];
-                X = m2 > 0.f ? cscale(X, fmaf(cp * av[j], rs, b * inv_m) * inv_m)
-                             : make_float2(cp * av[j] * inv_m, 0.f);
-            }
-        }
-
+        raar_fourier_phase<M>(a, fo, v, acc);
         G::inverse(v, S, tw);
 
         fence_proxy_async_smem();
@@ -193,24 +235,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
             if (tid == 0) issue_c(nxt);
             c_pending = true;
         }
-
-        // ---------------------------------------------- epilogue: store, scatter
-#pragma unroll
-        for (int k0 = 0; k0 < 32; k0 += CH) {
-            float2 wp[CH];
-#pragma unroll
-            for (int k = k0; k < k0 + CH; ++k) wp[k - k0] = ld_hint(a.w_proj + (q + TX * k) * M + x, pol_keep);
-#pragma unroll
-            for (int k = k0; k < k0 + CH; ++k) {
-                const int y = q + TX * k;
-                const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
-                const float2 cn = v[k];
-                st_hint(a.c + fo + y * M + x, cn, pol_stream);
-                red_hint(a.accA + o, cmulc(wp[k - k0], cn), pol_keep);
-                if (a.write_e) red_hint(a.ebuf + fo + y * M + x, cn, pol_stream);
-            }
-            chunk_fence_r();
-        }
+        raar_epilogue<M, WRAP>(a, py, px, fo, v, pol_stream, pol_keep);
         cur = nxt;
     }
 
@@ -225,6 +250,166 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
     if (tid == 0) {
 #pragma unroll
         for (int j = 0; j < 5; ++j) atomicAdd(a.sums + j, (double)acc[j]);
+    }
+}
+
+// ------------------------------------------------------------------ batch
+// Frames of several independent scans of the same frame size in one
+// persistent launch.  Global frame g belongs to the scan s with
+// base[s] <= g < base[s+1]; the scan's arguments are copied to shared memory
+// when a block moves to a frame of another scan, and the block's metric sums
+// are flushed to the scan it leaves.  Scans may differ in everything but the
+// frame size and the step's flags (FORM_B / METRIC are compile-time).
+
+template <int M, int FLAGS>
+__global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_batch_kernel(const BatchTable bt) {
+    using G = Fft3<M>;
+    using R = RaarGeo<M>;
+    constexpr int NT = G::NT;
+    constexpr int MM = M * M;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2* S = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = reinterpret_cast<float2*>(smem_raw + R::S_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + R::S_BYTES + R::TW_BYTES);
+    __shared__ float red[32 * 5];
+    __shared__ FrameArgs sa;                  // arguments of the current scan
+    __shared__ int s_next, s_next_scan;
+    const int tid = threadIdx.x;
+
+    G::load_twiddles(tw);
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
+
+    auto scan_of = [&](int g) {               // thread 0 only
+        int s = 0;
+        while (s + 1 < bt.nscans && __ldg(bt.base + s + 1) <= g) ++s;
+        return s;
+    };
+    auto issue_c = [&](int g, int s) {        // thread 0 only
+        const FrameArgs& t = bt.scans[s];
+        const int f = g - __ldg(bt.base + s);
+        mbar_expect_tx(&bars[0], (unsigned)(MM * sizeof(float2)));
+        bulk_g2s_hint(S, t.c + (size_t)f * MM, (unsigned)(MM * sizeof(float2)), &bars[0], pol_stream);
+    };
+    if (tid == 0) {
+        __nanosleep(2000u * (blockIdx.x & 3u));
+        const int g = atomicAdd(bt.counter, 1);
+        s_next = g;
+        s_next_scan = g < bt.total ? scan_of(g) : 0;
+        if (g < bt.total) issue_c(g, s_next_scan);
+    }
+    __syncthreads();
+    int cur = s_next, cur_scan = s_next_scan, loaded_scan = -1;
+
+    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    unsigned par_c = 0;
+    bool c_pending = cur < bt.total;
+    bool ok = true;
+
+    auto flush = [&](int s) {                 // block-wide: metric sums to scan s
+        block_sum<NT, 5>(acc, red);
+        if (tid == 0) {
+#pragma unroll
+            for (int j = 0; j < 5; ++j) atomicAdd(bt.scans[s].sums + j, (double)acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 5; ++j) acc[j] = 0.f;
+    };
+
+    while (cur < bt.total) {
+        if (cur_scan != loaded_scan) {
+            if (loaded_scan >= 0) flush(loaded_scan);
+            __syncthreads();
+            if (tid == 0) sa = bt.scans[cur_scan];
+            __syncthreads();
+            loaded_scan = cur_scan;
+        }
+        const int i = cur - __ldg(bt.base + cur_scan);
+        if (tid == 0) {
+            const int g = atomicAdd(bt.counter, 1);
+            s_next = g;
+            s_next_scan = g < bt.total ? scan_of(g) : 0;
+        }
+        const int py = sa.pos[2 * i];
+        const int px = sa.pos[2 * i + 1];
+        const size_t fo = (size_t)i * MM;
+        float2 v[32];
+        if (tid == 0) bulk_prefetch_l2(sa.amp + fo, (unsigned)(MM * sizeof(float)));
+
+        ok = __syncthreads_and(mbar_wait(&bars[0], par_c));
+        if (!ok) break;
+        par_c ^= 1u;
+        c_pending = false;
+        const int nxt = s_next, nxt_scan = s_next_scan;
+
+        if (sa.wrap) raar_load_phase<M, FLAGS, 1>(sa, py, px, fo, S, v, acc, pol_stream, pol_keep);
+        else raar_load_phase<M, FLAGS, 0>(sa, py, px, fo, S, v, acc, pol_stream, pol_keep);
+        G::forward(v, S, tw);
+        raar_fourier_phase<M>(sa, fo, v, acc);
+        G::inverse(v, S, tw);
+
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (nxt < bt.total) {
+            if (tid == 0) issue_c(nxt, nxt_scan);
+            c_pending = true;
+        }
+        if (sa.wrap) raar_epilogue<M, 1>(sa, py, px, fo, v, pol_stream, pol_keep);
+        else raar_epilogue<M, 0>(sa, py, px, fo, v, pol_stream, pol_keep);
+        cur = nxt;
+        cur_scan = nxt_scan;
+    }
+
+    if (!ok) {
+        if (c_pending) mbar_wait(&bars[0], par_c);
+        if (tid == 0) {
+            atomicExch(bt.err, SHARP_ERR_TIMEOUT);
+            atomicExch(bt.scans[cur_scan].err, SHARP_ERR_TIMEOUT);   // the scan's plan status
+        }
+        return;
+    }
+    if (loaded_scan >= 0) flush(loaded_scan);
+}
+
+template <int M, int FLAGS>
+static cudaError_t launch_raar_batch_one(const BatchTable& bt, int grid, cudaStream_t s) {
+    using R = RaarGeo<M>;
+    auto kern = raar_batch_kernel<M, FLAGS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(bt.counter, 0, sizeof(int), s)) != cudaSuccess) return e;
+    kern<<<grid, Fft3<M>::NT, R::SMEM, s>>>(bt);
+    return cudaGetLastError();
+}
+
+// Largest useful grid of the batch kernel (resident blocks on the device).
+template <int M>
+cudaError_t raar_batch_max_grid(int* grid) {
+    using R = RaarGeo<M>;
+    auto kern = raar_batch_kernel<M, 0>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Fft3<M>::NT, R::SMEM)) != cudaSuccess)
+        return e;
+    *grid = sms * (per_sm < 1 ? 1 : per_sm);
+    return cudaSuccess;
+}
+
+template <int M>
+cudaError_t launch_raar_batch_m(int flags, const BatchTable& bt, int grid, cudaStream_t s) {
+    switch (flags & (RF_FORM_B | RF_METRIC)) {
+        case 0: return launch_raar_batch_one<M, 0>(bt, grid, s);
+        case RF_FORM_B: return launch_raar_batch_one<M, RF_FORM_B>(bt, grid, s);
+        case RF_METRIC: return launch_raar_batch_one<M, RF_METRIC>(bt, grid, s);
+        default: return launch_raar_batch_one<M, RF_FORM_B | RF_METRIC>(bt, grid, s);
     }
 }
 

@@ -14,10 +14,6 @@
 
 using sharp::Plan;
 
-struct sharp_plan_s {
-    Plan p;
-};
-
 namespace {
 
 // Kernel timing: an event pair per launch, read back on demand.
@@ -114,6 +110,99 @@ int check_plan(sharp_plan plan) {
 }  // namespace
 
 void sharp::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+cudaError_t sharp::raar_step_clear(Plan& p, cudaStream_t s) {
+    return cudaMemsetAsync(p.sums, 0, 8 * sizeof(double), s);
+}
+
+int sharp::raar_step_prepare(Plan& p, float2* state_c, float2* psi_y, float2* psi, const float* amp, int iter,
+                             sharp::FrameArgs* out, sharp::StepInfo* info) {
+    SHARP_NONNULL(state_c); SHARP_NONNULL(psi_y); SHARP_NONNULL(psi); SHARP_NONNULL(amp);
+    if (!p.initialised) return fail(SHARP_ERR_STATE, "RAAR step before sharp_raar_init");
+    if ((reinterpret_cast<uintptr_t>(state_c) | reinterpret_cast<uintptr_t>(amp)) & 15)
+        return fail(SHARP_ERR_INVALID_ARG, "state_c and amp must be 16-byte aligned (bulk copies)");
+    if (iter < 1) return fail(SHARP_ERR_INVALID_ARG, "iter = %d < 1", iter);
+    const size_t mm = (size_t)p.m * p.m;
+    const int R = p.prm.residual_every;
+    const bool cadence = R > 0 && iter % R == 0;
+    sharp::StepInfo in;
+    std::memset(&in, 0, sizeof(in));
+    in.write_e = (R > 0 && (iter + 1) % R == 0) ? 1 : 0;
+    if (!p.b_valid) in.flags |= sharp::RF_FORM_B;
+    if (cadence) {
+        in.flags |= sharp::RF_METRIC;
+        in.have_q = 1;
+        if (p.last_iter == 0) {
+            in.have_d = 1;
+            in.delta_is_norm = 1;   // z^(-1) = 0
+        } else if (p.e_written_iter == iter - 1 && p.last_iter == iter - 1) {
+            in.have_d = 1;
+            in.read_e = 1;
+        }
+    }
+    in.probe_due = (p.prm.probe_every > 0 && iter % p.prm.probe_every == 0) ? 1 : 0;
+    if ((in.read_e || in.write_e) && !p.ebuf) {
+        SHARP_CK(dalloc(&p.ebuf, (size_t)p.K * mm));
+    }
+    sharp::FrameArgs a = base_args(p);
+    a.c = state_c;
+    a.psiy = psi_y;
+    a.psi = psi;
+    a.ebuf = p.ebuf;
+    a.w_form = p.w_form;
+    a.w_proj = p.w_cur;
+    a.accA = p.accA;
+    a.accB = p.accB;
+    a.amp = amp;
+    a.read_e = in.read_e;
+    a.write_e = in.write_e;
+    *out = a;
+    *info = in;
+    return SHARP_OK;
+}
+
+int sharp::raar_step_finish(Plan& p, float2* state_c, float2* psi_y, float2* psi, float2* probe, double* metrics,
+                            int iter, const sharp::StepInfo& in, cudaStream_t s, bool record_times, int mode) {
+    void* prof = p.prof;
+    if (!record_times) p.prof = nullptr;
+    const size_t mm = (size_t)p.m * p.m;
+    const int form_b = (in.flags & sharp::RF_FORM_B) ? 1 : 0;
+    int rc = SHARP_OK;
+    const bool dry = mode == 1;
+    auto ck = [&](cudaError_t e, const char* what) {
+        if (e != cudaSuccess && rc == SHARP_OK) rc = fail(SHARP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    };
+    // in bookkeeping-only mode every launch below is skipped
+    auto timed_or_skip = [&](int cls, int kernels, auto body) -> cudaError_t {
+        return dry ? cudaSuccess : timed(p, cls, kernels, s, body);
+    };
+    ck(timed_or_skip(K_IMAGE, 1, [&] { return sharp::launch_normalise(p, psi_y, psi, form_b, s); }), "normalise");
+    p.b_valid = true;   // Q* z^(l) / D = psi^(l) for the next step
+    if (p.form_differs) {
+        if (!dry)
+            ck(cudaMemcpyAsync(p.w_form, p.w_cur, mm * sizeof(float2), cudaMemcpyDeviceToDevice, s), "probe copy");
+        p.form_differs = false;
+    }
+    if (metrics)
+        ck(timed_or_skip(K_OTHER, 1, [&] {
+               return sharp::launch_metrics_finalize(p, metrics, in.have_q, in.have_d, in.delta_is_norm, s);
+           }), "metrics");
+    if (in.probe_due) {
+        ck(timed_or_skip(K_PROBE, 3, [&] { return sharp::launch_probe_update_state(p, state_c, psi_y, psi, s); }),
+           "probe update");
+        ck(timed_or_skip(K_ILLUM, 3, [&] {
+               return sharp::launch_illumination(p, p.w_cur, p.w2, p.Dsum, p.invD, p.dmax_bits, s);
+           }), "illumination");
+        p.b_valid = false;
+        p.form_differs = true;
+    }
+    if (probe && !dry)
+        ck(cudaMemcpyAsync(probe, p.w_cur, mm * sizeof(float2), cudaMemcpyDeviceToDevice, s), "probe out");
+    p.e_written_iter = in.write_e ? iter : 0;
+    p.last_iter = iter;
+    p.prof = prof;
+    return rc;
+}
 
 extern "C" {
 
@@ -360,70 +449,13 @@ int sharp_raar_init(sharp_plan plan, const float2* psi0, const float2* probe0, f
 int sharp_raar_step(sharp_plan plan, float2* state_c, float2* psi_y, float2* psi, float2* probe, const float* amp,
                     double* metrics, int iter, cudaStream_t s) {
     if (int r = check_plan(plan)) return r;
-    SHARP_NONNULL(state_c); SHARP_NONNULL(psi_y); SHARP_NONNULL(psi); SHARP_NONNULL(amp);
     Plan& p = plan->p;
-    if (!p.initialised) return fail(SHARP_ERR_STATE, "sharp_raar_step before sharp_raar_init");
-    if ((reinterpret_cast<uintptr_t>(state_c) | reinterpret_cast<uintptr_t>(amp)) & 15)
-        return fail(SHARP_ERR_INVALID_ARG, "state_c and amp must be 16-byte aligned (bulk copies)");
-    if (iter < 1) return fail(SHARP_ERR_INVALID_ARG, "iter = %d < 1", iter);
-    const size_t mm = (size_t)p.m * p.m;
-    const int R = p.prm.residual_every;
-    const bool cadence = R > 0 && iter % R == 0;
-    const bool write_e = R > 0 && (iter + 1) % R == 0;
-    int flags = 0;
-    if (!p.b_valid) flags |= sharp::RF_FORM_B;
-    int have_q = 0, have_d = 0, delta_is_norm = 0, read_e = 0;
-    if (cadence) {
-        flags |= sharp::RF_METRIC;
-        have_q = 1;
-        if (p.last_iter == 0) {
-            have_d = 1;
-            delta_is_norm = 1;   // z^(-1) = 0
-        } else if (p.e_written_iter == iter - 1 && p.last_iter == iter - 1) {
-            have_d = 1;
-            read_e = 1;
-        }
-    }
-    if ((read_e || write_e) && !p.ebuf) {
-        SHARP_CK(dalloc(&p.ebuf, (size_t)p.K * mm));
-    }
-    SHARP_CK(cudaMemsetAsync(p.sums, 0, 8 * sizeof(double), s));
-    sharp::FrameArgs a = base_args(p);
-    a.c = state_c;
-    a.psiy = psi_y;
-    a.psi = psi;
-    a.ebuf = p.ebuf;
-    a.w_form = p.w_form;
-    a.w_proj = p.w_cur;
-    a.accA = p.accA;
-    a.accB = p.accB;
-    a.amp = amp;
-    a.read_e = read_e;
-    a.write_e = write_e ? 1 : 0;
-    SHARP_CK(timed(p, K_FRAME, 1, s, [&] { return sharp::launch_frames(sharp::MODE_RAAR, flags, a, s); }));
-    const int form_b = (flags & sharp::RF_FORM_B) ? 1 : 0;
-    SHARP_CK(timed(p, K_IMAGE, 1, s, [&] { return sharp::launch_normalise(p, psi_y, psi, form_b, s); }));
-    p.b_valid = true;   // Q* z^(l) / D = psi^(l) for the next step
-    if (p.form_differs) {
-        SHARP_CK(cudaMemcpyAsync(p.w_form, p.w_cur, mm * sizeof(float2), cudaMemcpyDeviceToDevice, s));
-        p.form_differs = false;
-    }
-    if (metrics)
-        SHARP_CK(timed(p, K_OTHER, 1, s, [&] {
-            return sharp::launch_metrics_finalize(p, metrics, have_q, have_d, delta_is_norm, s);
-        }));
-    if (p.prm.probe_every > 0 && iter % p.prm.probe_every == 0) {
-        SHARP_CK(timed(p, K_PROBE, 3, s, [&] { return sharp::launch_probe_update_state(p, state_c, psi_y, psi, s); }));
-        SHARP_CK(timed(p, K_ILLUM, 3, s, [&] {
-            return sharp::launch_illumination(p, p.w_cur, p.w2, p.Dsum, p.invD, p.dmax_bits, s);
-        }));
-        p.b_valid = false;
-        p.form_differs = true;
-    }
-    if (probe) SHARP_CK(cudaMemcpyAsync(probe, p.w_cur, mm * sizeof(float2), cudaMemcpyDeviceToDevice, s));
-    p.e_written_iter = write_e ? iter : 0;
-    p.last_iter = iter;
-    return SHARP_OK;
+    sharp::FrameArgs a;
+    sharp::StepInfo info;
+    if (int r = sharp::raar_step_prepare(p, state_c, psi_y, psi, amp, iter, &a, &info)) return r;
+    SHARP_CK(sharp::raar_step_clear(p, s));
+    SHARP_CK(timed(p, K_FRAME, 1, s, [&] { return sharp::launch_frames(sharp::MODE_RAAR, info.flags, a, s); }));
+    return sharp::raar_step_finish(p, state_c, psi_y, psi, probe, metrics, iter, info, s, true);
 }
 
 int sharp_solution_error(sharp_plan plan, const float2* psi, const float2* psi_true, const float2* probe,

@@ -194,6 +194,40 @@ cudaError_t launch_copy_scaled(const double* src, double* dst, double scale, cud
 // Message returned by sharp_last_error() on this thread (sharp_api.cu).
 void set_last_error(const char* msg);
 
+// Host-side schedule of one RAAR step of a plan (what the launches need).
+struct StepInfo {
+    int flags;           // RF_FORM_B | RF_METRIC
+    int have_q, have_d, delta_is_norm, read_e, write_e, probe_due;
+};
+// sharp_api.cu: argument/state checks, scratch setup and the frame-pass
+// arguments of step `iter`.  No GPU work is queued (the step's sums are
+// cleared by raar_step_clear).
+int raar_step_prepare(Plan& p, float2* c, float2* psiy, float2* psi, const float* amp, int iter, FrameArgs* a,
+                      StepInfo* info);
+cudaError_t raar_step_clear(Plan& p, cudaStream_t s);
+// Launches after the frame pass (image pass, metrics, probe update) and the
+// plan's bookkeeping.  mode 0: launch and update the bookkeeping; mode 1:
+// bookkeeping only (a recorded graph issues the launches).  With
+// `record_times` false no timing events are used.
+int raar_step_finish(Plan& p, float2* c, float2* psiy, float2* psi, float2* probe, double* metrics, int iter,
+                     const StepInfo& info, cudaStream_t s, bool record_times, int mode = 0);
+
+// Batch frame pass (raar_batch_64.cu, raar_batch_128.cu)
+// Frames of several scans in one persistent launch: scan s owns global frame
+// indices base[s] .. base[s+1]-1.
+struct BatchTable {
+    const FrameArgs* scans;   // device array, one per scan
+    const int* base;          // device array, nscans + 1 prefix sums of K
+    int nscans;
+    int total;                // base[nscans]
+    int* counter;             // global frame counter (zeroed per launch)
+    int* err;                 // batch status; a timeout also sets the scan's plan flag
+};
+template <int M>
+cudaError_t launch_raar_batch_m(int flags, const BatchTable& bt, int grid, cudaStream_t s);
+template <int M>
+cudaError_t raar_batch_max_grid(int* grid);
+
 // slots of Plan::sums
 enum SumSlot {
     S_RESID = 0,   // sum (a - |Fz|)^2  = ||P_a z - z||^2
@@ -204,3 +238,8 @@ enum SumSlot {
 };
 
 }  // namespace sharp
+
+// The opaque handle of the C ABI.
+struct sharp_plan_s {
+    sharp::Plan p;
+};
