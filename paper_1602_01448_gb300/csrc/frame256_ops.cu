@@ -1,0 +1,17 @@
+// Standalone frame operators for 256x256 frames: P_a of explicit frames
+// (Eq. 7), the forward model (Eq. 1), the amplitude loss and its adjoint.
+#include "frame256.cuh"
+
+namespace sharp {
+
+cudaError_t launch_big_ops(int mode, const FrameArgs& a, cudaStream_t s) {
+    switch (mode) {
+        case MODE_PROJECT: return big_launch<MODE_PROJECT, 0>(a, nullptr, 0, a.scratch, s);
+        case MODE_AMPS: return big_launch<MODE_AMPS, 0>(a, nullptr, 0, a.scratch, s);
+        case MODE_LOSS: return big_launch<MODE_LOSS, 0>(a, nullptr, 0, a.scratch, s);
+        case MODE_GRAD: return big_launch<MODE_GRAD, 0>(a, nullptr, 0, a.scratch, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace sharp

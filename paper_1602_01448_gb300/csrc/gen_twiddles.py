@@ -42,7 +42,7 @@ def main():
         out.append("    return 0.0f;")
         out.append("}")
     out.append("")
-    for m in (64, 128, 256):
+    for m in (64, 128):
         tx, tt, x0 = geometry(m)
         vals = []
         for q in range(tx):
@@ -57,6 +57,13 @@ def main():
         out.append(f"// tw2_{m}[x0*{tt} + t] = W_{m}^(x0 t), x0 < {x0}")
         out.append(f"__constant__ float2 c_tw2_{m}[{x0 * tt}] = {{" + ", ".join(vals) + "};")
         out.append("")
+    vals = []
+    for k in range(16):
+        for j in range(16):
+            vals.append("{%s, %s}" % root(256, j * k))
+    out.append("// tw256x16[k*16 + j] = W_256^(j k), j, k < 16 (256 = 16 x 16 line transforms)")
+    out.append("__constant__ float2 c_tw256x16[256] = {" + ", ".join(vals) + "};")
+    out.append("")
     out.append("}  // namespace sharp")
     with open("twiddle_tables.cuh", "w") as f:
         f.write("\n".join(out) + "\n")

@@ -74,13 +74,13 @@ cudaError_t dalloc(T** p, size_t count) {
     return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
-bool supported_m(int m) { return m == 64 || m == 128; }
+bool supported_m(int m) { return m == 64 || m == 128 || m == 256; }
 
 void free_plan(Plan& p) {
     void* ptrs[] = {p.pos,   p.tile_ptr,   p.tile_frames, p.w_cur, p.w_form,     p.w2,
                     p.Dsum,  p.invD,       p.dmax_bits,   p.accA,  p.accB,       p.ebuf,
                     p.sums,  p.probe_part, p.probe_acc,   p.scal,  p.w2tmp,      p.Dtmp,
-                    p.invDtmp, p.errflag, p.counter};
+                    p.invDtmp, p.errflag, p.counter, p.big_scratch};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     std::memset(&p, 0, sizeof(p));
@@ -98,6 +98,7 @@ sharp::FrameArgs base_args(const Plan& p) {
     a.beta = p.prm.beta;
     a.sums = p.sums;
     a.err = p.errflag;
+    a.scratch = p.big_scratch;
     a.counter = p.counter;
     return a;
 }
@@ -227,7 +228,7 @@ int sharp_plan_create(sharp_plan* out, int K, int m, int ny, int nx, const int32
     SHARP_NONNULL(pos);
     if (K < 1) return fail(SHARP_ERR_INVALID_ARG, "K = %d < 1", K);
     if (m < 1 || ny < m || nx < m) return fail(SHARP_ERR_INVALID_ARG, "need 1 <= m <= ny, nx (m=%d ny=%d nx=%d)", m, ny, nx);
-    if (!supported_m(m)) return fail(SHARP_ERR_UNSUPPORTED_SIZE, "frame size m=%d has no kernel (64, 128)", m);
+    if (!supported_m(m)) return fail(SHARP_ERR_UNSUPPORTED_SIZE, "frame size m=%d has no kernel (64, 128, 256)", m);
     if ((long long)ny * nx > (1LL << 30) || (long long)K * m * m > (1LL << 34))
         return fail(SHARP_ERR_INVALID_ARG, "problem too large for 32-bit pixel indexing");
     sharp_params prm;
@@ -304,6 +305,12 @@ int sharp_plan_create(sharp_plan* out, int K, int m, int ny, int nx, const int32
     SHARP_ALLOC(invDtmp, n)
     SHARP_ALLOC(errflag, 1)
     SHARP_ALLOC(counter, 1)
+    if (m == 256) {   // one frame slab per SM for the line-pass transform
+        int dev = 0, sms = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        SHARP_ALLOC(big_scratch, (size_t)sms * mm)
+    }
 #undef SHARP_ALLOC
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.pos, hpos.data(), hpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.tile_ptr, count.data(), count.size() * sizeof(int), cudaMemcpyHostToDevice, stream);

@@ -37,6 +37,7 @@ struct Group {                    // scans of one frame size
     std::vector<int> scans;       // indices into the batch
     int total = 0;
     int* d_base = nullptr;
+    float2* slab = nullptr;       // 256^2 frames: one frame of scratch per block
     int max_grid = 0;
     std::vector<int> candidates;  // grid candidates (autotuner)
     std::vector<float> cand_ms;
@@ -84,6 +85,18 @@ cudaError_t group_launch(const Group& g, const sharp::FrameArgs* table, int flag
 
 cudaError_t launch_group(const Group& g, const sharp::FrameArgs* table, int flags, int grid, int* counter, int* err,
                          cudaStream_t s) {
+    if (g.m == 256) {
+        sharp::BatchTable bt;
+        bt.scans = table;
+        bt.base = g.d_base;
+        bt.nscans = (int)g.scans.size();
+        bt.total = g.total;
+        bt.counter = counter;
+        bt.err = err;
+        sharp::FrameArgs none;
+        memset(&none, 0, sizeof(none));
+        return sharp::launch_big_raar(flags, none, &bt, grid, g.slab, s);
+    }
     return g.m == 64 ? group_launch<64>(g, table, flags, grid, counter, err, s)
                      : group_launch<128>(g, table, flags, grid, counter, err, s);
 }
@@ -113,7 +126,10 @@ int sharp_batch_create(sharp_batch* out, int nscans, const sharp_plan* plans) {
     sharp_batch b = new sharp_batch_s;
     b->plans.assign(plans, plans + nscans);
     b->binds.resize(nscans);
-    for (int m : {64, 128}) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int m : {64, 128, 256}) {
         Group g;
         g.m = m;
         for (int i = 0; i < nscans; ++i)
@@ -124,15 +140,20 @@ int sharp_batch_create(sharp_batch* out, int nscans, const sharp_plan* plans) {
         g.total = base.back();
         cudaError_t e = cudaMalloc(&g.d_base, base.size() * sizeof(int));
         if (e == cudaSuccess) e = cudaMemcpy(g.d_base, base.data(), base.size() * sizeof(int), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = (m == 64) ? sharp::raar_batch_max_grid<64>(&g.max_grid)
-                                            : sharp::raar_batch_max_grid<128>(&g.max_grid);
+        if (e == cudaSuccess) {
+            if (m == 256) {
+                g.max_grid = sms;   // one block (and one slab) per SM
+                e = cudaMalloc(&g.slab, (size_t)sms * m * m * sizeof(float2));
+            } else {
+                e = (m == 64) ? sharp::raar_batch_max_grid<64>(&g.max_grid)
+                              : sharp::raar_batch_max_grid<128>(&g.max_grid);
+            }
+        }
         if (e != cudaSuccess) {
+            b->groups.push_back(g);   // freed by destroy
             sharp_batch_destroy(b);
             return bfail(SHARP_ERR_CUDA, cudaGetErrorString(e));
         }
-        int dev = 0, sms = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         for (int k = 1; k * sms <= g.max_grid; ++k) g.candidates.push_back(k * sms);
         if (g.candidates.empty()) g.candidates.push_back(g.max_grid);
         g.cand_ms.assign(g.candidates.size(), -1.f);
@@ -320,8 +341,10 @@ int sharp_batch_destroy(sharp_batch b) {
     if (!b) return SHARP_OK;
     cudaDeviceSynchronize();
     drop_schedules(b);
-    for (auto& g : b->groups)
+    for (auto& g : b->groups) {
         if (g.d_base) cudaFree(g.d_base);
+        if (g.slab) cudaFree(g.slab);
+    }
     if (b->counter) cudaFree(b->counter);
     if (b->err) cudaFree(b->err);
     if (b->cap) cudaStreamDestroy(b->cap);

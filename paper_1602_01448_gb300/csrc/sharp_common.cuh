@@ -113,6 +113,7 @@ struct Plan {
     void* prof;              // kernel-timing state (sharp_api.cu), nullptr when off
     int* errflag;            // device int: sticky error raised inside kernels
     int* counter;            // device int: work counter of the persistent frame pass
+    float2* big_scratch;     // m = 256: one m*m slab per SM (frame transposition)
 };
 
 constexpr int TILE = 32;
@@ -149,6 +150,7 @@ struct FrameArgs {
     double* sums;            // per-mode accumulators
     int* err;                // device error flag (SHARP_ERR_TIMEOUT on a bounded-wait failure)
     int* counter;            // frame counter of the persistent RAAR pass (zeroed per launch)
+    float2* scratch;         // 256^2 frames: one m*m slab per block of the frame kernels
 };
 
 // compile-time flags of MODE_RAAR
@@ -163,11 +165,22 @@ inline cudaError_t launch_raar_m(int flags, const FrameArgs& a, cudaStream_t s) 
     return a.wrap ? launch_raar_w<M, 1>(flags, a, s) : launch_raar_w<M, 0>(flags, a, s);
 }
 
+// 256^2 frames (frame256_raar.cu, frame256_ops.cu): the RAAR pass for one
+// scan (bt null) or a batch, and the standalone modes; slabs of m*m scratch,
+// one per block, at most one block per SM.
+struct BatchTable;
+cudaError_t launch_big_raar(int flags, const FrameArgs& a, const BatchTable* bt, int grid, float2* slab,
+                            cudaStream_t s);
+cudaError_t launch_big_ops(int mode, const FrameArgs& a, cudaStream_t s);
+
 inline cudaError_t launch_frames(int mode, int flags, const FrameArgs& a, cudaStream_t s) {
     if (a.K <= 0) return cudaSuccess;
     switch (a.m) {
         case 64: return launch_frames_m<64>(mode, flags, a, s);
         case 128: return launch_frames_m<128>(mode, flags, a, s);
+        case 256:
+            return mode == MODE_RAAR ? launch_big_raar(flags, a, nullptr, 0, a.scratch, s)
+                                     : launch_big_ops(mode, a, s);
     }
     return cudaErrorInvalidValue;
 }

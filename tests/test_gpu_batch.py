@@ -25,7 +25,8 @@ TOL = 2e-5          # relative L2 per step, FP32 rounding of a reordered sum
 def _scans():
     out = [synth.scan_batch_member(11, 64, 30), synth.scan_batch_member(12, 128, 12),
            synth.scan_batch_member(13, 64, 17),
-           synth.scan_wrapped_raster(seed=14, side=6, m=64, n=128, step=20, photons=1e6)]
+           synth.scan_wrapped_raster(seed=14, side=6, m=64, n=128, step=20, photons=1e6),
+           synth.scan_batch_member(15, 256, 7), synth.scan_batch_member(16, 256, 4)]
     return out
 
 
@@ -86,10 +87,10 @@ def _run(use_graphs, n_steps=8):
 def test_batch_with_graphs_matches_scans_run_alone():
     batch = _run(True)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    for m in (64, 128):
+    for m in (64, 128, 256):
         g = batch.tuned_grid(m)
         assert g > 0 and g % sms == 0, (m, g)
-    assert batch.tuned_grid(256) == -1
+    assert batch.tuned_grid(32) == -1
     batch.close()
 
 

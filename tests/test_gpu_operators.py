@@ -33,7 +33,7 @@ def _case(m, wrap, seed=0):
     return pos, obj, w, (ny, nx)
 
 
-@pytest.mark.parametrize("m", [64, 128])
+@pytest.mark.parametrize("m", [64, 128, 256])
 @pytest.mark.parametrize("wrap", [False, True])
 def test_split_forward_model_and_overlap(m, wrap):
     S = _lib()
@@ -50,7 +50,7 @@ def test_split_forward_model_and_overlap(m, wrap):
     assert rel_l2(host(zo), O.split(ref_psi, w, pos, wrap)) < TOL
 
 
-@pytest.mark.parametrize("m", [64, 128])
+@pytest.mark.parametrize("m", [64, 128, 256])
 def test_fourier_projection(m):
     S = _lib()
     pos, obj, w, shape = _case(m, False)
@@ -69,7 +69,7 @@ def test_fourier_projection(m):
     assert rel_l2(host(zt), ref) < TOL
 
 
-@pytest.mark.parametrize("m", [64, 128])
+@pytest.mark.parametrize("m", [64, 128, 256])
 @pytest.mark.parametrize("wrap", [False, True])
 def test_probe_update(m, wrap):
     S = _lib()
@@ -90,7 +90,7 @@ def test_probe_update_fixed_point_at_truth():
     assert rel_l2(got, w) < 1e-6
 
 
-@pytest.mark.parametrize("m", [64, 128])
+@pytest.mark.parametrize("m", [64, 128, 256])
 def test_amp_loss_and_adjoint(m):
     S = _lib()
     pos, obj, w, shape = _case(m, False, seed=4)
@@ -147,7 +147,7 @@ def test_bad_arguments_are_rejected():
         S.sharp_plan_create(2, 64, 256, 256, pos)
     assert e.value.code == 1
     with pytest.raises(S.SharpError) as e:
-        S.sharp_plan_create(2, 256, 512, 512, dev(np.zeros((2, 2), np.int32)))
+        S.sharp_plan_create(2, 96, 512, 512, dev(np.zeros((2, 2), np.int32)))
     assert e.value.code == 2
     plan = S.Plan(np.zeros((1, 2), np.int32), 64, (64, 64))
     with pytest.raises(S.SharpError) as e:

@@ -41,7 +41,7 @@ def _check_metrics(gpu, rec, first):
     assert abs(gpu[2] - rec["eps_delta"]) <= 1e-4 * rec["eps_delta"] + 2e-6
 
 
-@pytest.mark.parametrize("m,side,step", [(64, 5, 12), (128, 4, 24)])
+@pytest.mark.parametrize("m,side,step", [(64, 5, 12), (128, 4, 24), (256, 3, 48)])
 def test_raar_steps_match_oracle(m, side, step):
     S = _lib()
     obj, w, pos, shape, a = _noisy_scan(m, side, step, 37, seed=m)
