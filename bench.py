@@ -37,7 +37,8 @@ METRIC = "RAAR frame-iterations/s on 1 GB300 (FP32 vs mixed) and % of HBM roofli
 UNIT = "frame-iterations/s"
 WORKLOAD = "fermat-2500x128-obj1024"
 RESIDUAL_EVERY = 10   # eps_Q and eps_Delta every 10th step; eps_a every step
-PROFILE = os.path.join(ROOT, "profiles", "frame_kernel_fermat2500x128.txt")
+PROFILES = {"fermat": os.path.join(ROOT, "profiles", "raar_kernel_fermat128.txt"),
+            "raster256": os.path.join(ROOT, "profiles", "big_kernel_raster256.txt")}
 CSRC = os.path.join(ROOT, "paper_1602_01448_gb300", "csrc")
 
 
@@ -50,11 +51,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(workload: str = "fermat"):
     """DRAM bytes per launch of the frame kernel from the committed ncu
     summary, or None when the kernel sources changed since it was taken."""
     try:
-        text = open(PROFILE).read()
+        text = open(PROFILES[workload]).read()
     except OSError:
         return None
     mh = re.search(r"source_hash:\s*([0-9a-f]+)", text)
@@ -141,11 +142,12 @@ def job_throughput(frames_per_rank: int, steps: int, world: int, ms_total: float
     return world * frames_per_rank * steps / (ms_total / 1000.0)
 
 
-def make_scan(frames: int = 2500, workload: str = "fermat"):
+def make_scan(frames=None, workload: str = "fermat"):
     import synth
     if workload == "raster256":
-        return synth.scan_large_raster()
-    return synth.scan_fermat(count=frames)
+        side = 100 if frames is None else max(1, int(round(math.sqrt(frames))))
+        return synth.scan_large_raster(side=side)
+    return synth.scan_fermat(count=2500 if frames is None else frames)
 
 
 def device_poisson(amp, photons: float, seed: int):
@@ -325,7 +327,7 @@ def run_ours(args, rank, world):
                    "l2": f"inputs larger than L2 (c {8 * K * m * m / 1e6:.0f} MB + a {4 * K * m * m / 1e6:.0f} MB per step)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": profiled_traffic() if args.workload == "fermat" else None,
+                     "traffic": profiled_traffic(args.workload) if args.frames is None else None,
                      "kernel": "raar_kernel<128>" if m <= 128 else "big_kernel<RAAR> (256^2 line passes)",
                      "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes, "kernel_ms": t_frame * 1000.0},
@@ -348,8 +350,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fermat", choices=["fermat", "raster256"])
-    ap.add_argument("--frames", type=int, default=2500,
-                    help="frames of the Fermat scan (2500 = the benchmark; fewer for small ncu captures)")
+    ap.add_argument("--frames", type=int, default=None,
+                    help="frames of the scan (default: the workload's; fewer for small ncu captures; "
+                         "raster256 rounds to a square raster)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
