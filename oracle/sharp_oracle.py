@@ -30,6 +30,20 @@ Readings of the paper taken here (each also listed in the design notes):
       metric of an iterate uses the projector of the probe that formed it;
       eps_Delta of the first step compares with a zero iterate.
   R8  eps_0 (Eq. 14) uses the closed-form optimal global phase.
+  R12 Illumination drift (Sec. 2.2 pathologies; sequence step 7): the centre
+      of mass is the |w|^2-weighted mean of the frame indices; the frame
+      centre is index m/2 per axis; the shift is d = floor(c - m/2 + 1/2)
+      and w is rolled by -d (periodic within the frame).  The object follows
+      by itself: the next object update uses the shifted probe.
+  R13 Illumination Fourier constraints (sequence step 7): F is the unitary
+      transform of Eq. 2; a mask multiplies Fw, amplitudes a_w replace |Fw|
+      (phase 1 where Fw = 0, as R3).  Order: Eq. 10, constraint, centring.
+  R14 Initial illumination (sequence step 2; Sec. 4 variant): the average
+      frame is the mean over frames of a_i^2 on the unitary scale; its
+      square root is inverse-transformed and centred in the frame (rolled
+      by m/2, i.e. the spectrum multiplied by (-1)^(qy+qx)).  With a
+      threshold t in (0, 1], values below t * max go to 0 and the others to
+      the mean of the values at or above it.
 
 Parity is pinned for every function below (see tests/test_oracle_*.py) except
 where a docstring says "parity unpinned".
@@ -262,14 +276,79 @@ def forward_amplitudes(psi, w, pos, wrap=False):
 # --------------------------------------------------------------------------
 # Reconstruction loop (Sec. 2.2 reconstruction sequence)
 # --------------------------------------------------------------------------
+# --------------------------------------------------------------------------
+# Sec. 2.2 -- illumination pathologies and initialisation (reconstruction
+# sequence steps 2 and 7; the threshold variant of Sec. 4)
+# --------------------------------------------------------------------------
+def probe_centroid(w):
+    """Centre of mass (row, col) of |w|^2 over frame indices 0..m-1 (R12)."""
+    inten = np.abs(np.asarray(w, dtype=np.complex128)) ** 2
+    m = inten.shape[0]
+    idx = np.arange(m, dtype=np.float64)
+    total = inten.sum()
+    row = float((inten.sum(axis=1) * idx).sum() / total)
+    col = float((inten.sum(axis=0) * idx).sum() / total)
+    return row, col
+
+
+def probe_center(w):
+    """Drift correction: roll w within the frame so that the centre of mass
+    of |w|^2 moves to the frame centre m/2 (R12).  Returns (w, (dy, dx))."""
+    w = np.asarray(w, dtype=np.complex128)
+    m = w.shape[0]
+    cy, cx = probe_centroid(w)
+    dy = int(np.floor(cy - m / 2 + 0.5))
+    dx = int(np.floor(cx - m / 2 + 0.5))
+    return np.roll(w, (-dy, -dx), axis=(0, 1)), (dy, dx)
+
+
+def probe_fourier_mask(w, mask):
+    """w <- F^-1{(F w) m_w} (sequence step 7, R13)."""
+    return ifft2u(fft2u(w) * np.asarray(mask, dtype=np.float64))
+
+
+def probe_fourier_amplitude(w, a_w):
+    """w <- F^-1{(F w)/|F w| a_w} (sequence step 7, R13; phase 1 where Fw = 0)."""
+    W = fft2u(w)
+    mag = np.abs(W)
+    phase = np.where(mag > 0, W / np.where(mag > 0, mag, 1.0), 1.0)
+    return ifft2u(np.asarray(a_w, dtype=np.float64) * phase)
+
+
+def probe_from_mean_frame(a, threshold=0.0):
+    """Initial illumination from the average frame (sequence step 2; with a
+    threshold, the variant of Sec. 4), centred in the frame (R14)."""
+    a = np.asarray(a, dtype=np.float64)
+    m = a.shape[-1]
+    mean = np.mean(a ** 2, axis=0)
+    if threshold > 0:
+        keep = mean >= threshold * mean.max()
+        mean = np.where(keep, mean[keep].mean(), 0.0)
+    w = ifft2u(np.sqrt(mean))
+    return np.roll(w, (m // 2, m // 2), axis=(0, 1))
+
+
+def refine_probe(w, probe_mask=None, probe_amp=None, probe_com=False):
+    """The steps after Eq. 10 in sequence step 7: the Fourier mask if given,
+    else the Fourier amplitudes if given, then the centring (R13, R12)."""
+    if probe_mask is not None:
+        w = probe_fourier_mask(w, probe_mask)
+    elif probe_amp is not None:
+        w = probe_fourier_amplitude(w, probe_amp)
+    if probe_com:
+        w, _ = probe_center(w)
+    return w
+
+
 def raar_reconstruct(a, pos, shape, w0, psi0, n_iter, beta=0.75, probe_every=0,
                      wrap=False, form="luke", psi_true=None, w_true=None,
-                     record_metrics=True):
+                     record_metrics=True, probe_mask=None, probe_amp=None, probe_com=False):
     """Run ``n_iter`` RAAR steps from z^(0) = Q psi^(0) with illumination w0.
 
     Step l (1-based): z^(l) = RAAR(z^(l-1)) with the current probe; then the
     object psi^(l) = Q*z^(l)/Q*Q (Eq. 9); then, when probe_every > 0 and
-    l % probe_every == 0, the probe from Eq. 10 using psi^(l) and z^(l).
+    l % probe_every == 0, the probe from Eq. 10 using psi^(l) and z^(l),
+    followed by the optional Fourier constraint and centring (``refine_probe``).
 
     Metrics recorded at step l describe z^(l-1), the iterate entering the step
     (reading R7): eps_a, eps_Q (projector of the probe that formed z^(l-1)),
@@ -295,6 +374,7 @@ def raar_reconstruct(a, pos, shape, w0, psi0, n_iter, beta=0.75, probe_every=0,
         psi = object_update(z_next, w, pos, shape, wrap)
         if probe_every and step % probe_every == 0:
             w = probe_update(z_next, psi, pos, w, wrap)
+            w = refine_probe(w, probe_mask, probe_amp, probe_com)
         if psi_true is not None:
             wt = w if w_true is None else w_true
             rec["eps_0"] = eps_0_object(psi, psi_true, wt, pos, shape, wrap)
