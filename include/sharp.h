@@ -126,6 +126,42 @@ int sharp_probe_update(sharp_plan plan, const float2* obj, const float2* z,
                        const float2* probe_old, float2* probe_out, cudaStream_t stream);
 
 /*
+ * Illumination refinement after each probe update (Sec. 2.2: the real-space
+ * drift and Fourier-space pathologies; reconstruction sequence step 7).
+ * With F the unitary transform of Eq. 2:
+ *   SHARP_PROBE_CONSTRAINT_MASK      : w <- F^-1{(F w) m_w}
+ *   SHARP_PROBE_CONSTRAINT_AMPLITUDE : w <- F^-1{a_w (F w)/|F w|}  (phase 1 where F w = 0)
+ * then, with center_of_mass != 0, w is rolled periodically within the frame
+ * by -d, d = floor(c - m/2 + 1/2) per axis, c the centre of mass of |w|^2 over
+ * frame indices 0..m-1 (the object follows through the next object update).
+ *   values : float[m][m] device array (mask or amplitudes), copied into the
+ *            plan; NULL with SHARP_PROBE_CONSTRAINT_NONE.
+ * sharp_plan_set_probe_refinement configures what sharp_raar_step (and the
+ * batch) applies after Eq. 10; sharp_probe_refine applies it to a given probe
+ * (probe_out may equal probe_in).  Set it before a batch records its steps.
+ * Errors: INVALID_ARG (unknown kind, values missing), CUDA.
+ */
+#define SHARP_PROBE_CONSTRAINT_NONE 0
+#define SHARP_PROBE_CONSTRAINT_MASK 1
+#define SHARP_PROBE_CONSTRAINT_AMPLITUDE 2
+int sharp_plan_set_probe_refinement(sharp_plan plan, int constraint, const float* values, int center_of_mass,
+                                    cudaStream_t stream);
+int sharp_probe_refine(sharp_plan plan, const float2* probe_in, float2* probe_out, cudaStream_t stream);
+
+/*
+ * Initial illumination from the average frame (Sec. 2.2 reconstruction
+ * sequence step 2; threshold variant of Sec. 4):
+ *   I(q)   = (1/K) sum_i amp_i(q)^2                (amplitudes on the unitary scale)
+ *   I'(q)  = I(q), or with 0 < threshold <= 1: 0 where I < threshold * max I and
+ *            the mean of the remaining values elsewhere
+ *   probe_out = F^-1 sqrt(I') rolled by m/2 per axis (centred in the frame).
+ *   amp : float[K][m][m];  probe_out : float2[m][m].
+ * Errors: INVALID_ARG (threshold outside [0, 1]), CUDA.
+ */
+int sharp_probe_init_mean(sharp_plan plan, const float* amp, float threshold, float2* probe_out,
+                          cudaStream_t stream);
+
+/*
  * Start a RAAR reconstruction from z^(0) = Q psi^(0) (Sec. 2.2 sequence).
  * The frames are kept implicitly as z = w_f . psi_y(r + x_i) + c_i, where w_f
  * is the probe that formed them; this call sets c = 0, psi_y = psi0, psi = psi0

@@ -77,6 +77,9 @@ _lib_fns = {
     "sharp_plan_set_profiling": ([_P, _I], _I),
     "sharp_plan_status": ([_P, _P], _I),
     "sharp_fourier_project_noalloc": ([_P, _P, _P, _P, _I, _I, _P], _I),
+    "sharp_plan_set_probe_refinement": ([_P, _I, _P, _I, _P], _I),
+    "sharp_probe_refine": ([_P, _P, _P, _P], _I),
+    "sharp_probe_init_mean": ([_P, _P, ctypes.c_float, _P, _P], _I),
     "sharp_batch_create": ([ctypes.POINTER(_P), _I, ctypes.POINTER(_P)], _I),
     "sharp_batch_bind": ([_P, _I, _P, _P, _P, _P, _P, _P], _I),
     "sharp_batch_step": ([_P, _I, _P], _I),
@@ -87,6 +90,11 @@ _lib_fns = {
     "sharp_plan_kernel_times": ([_P, _P, _P], _I),
 }
 _C = {name: _decl(name, *sig) for name, sig in _lib_fns.items()}
+
+
+SHARP_PROBE_CONSTRAINT_NONE = 0
+SHARP_PROBE_CONSTRAINT_MASK = 1
+SHARP_PROBE_CONSTRAINT_AMPLITUDE = 2
 
 
 def _check(code: int):
@@ -283,6 +291,29 @@ class Plan:
     def probe_update(self, obj, z, probe_old):
         out = torch.empty_like(probe_old)
         sharp_probe_update(self.handle, obj, z, probe_old, out)
+        return out
+
+    def set_probe_refinement(self, mask=None, amplitude=None, center=False, stream=None):
+        """What follows each probe update (Sec. 2.2 step 7): the Fourier mask
+        if given, else the Fourier amplitudes if given, then the centring."""
+        kind, vals = SHARP_PROBE_CONSTRAINT_NONE, None
+        if mask is not None:
+            kind, vals = SHARP_PROBE_CONSTRAINT_MASK, mask
+        elif amplitude is not None:
+            kind, vals = SHARP_PROBE_CONSTRAINT_AMPLITUDE, amplitude
+        ptr = None if vals is None else _f32(vals, "values", (self.m, self.m))
+        _check(_C["sharp_plan_set_probe_refinement"](self.handle, kind, ptr, int(bool(center)), _stream(stream)))
+
+    def probe_refine(self, probe, out=None):
+        out = torch.empty_like(probe) if out is None else out
+        _check(_C["sharp_probe_refine"](self.handle, _c64(probe, "probe", (self.m, self.m)),
+                                        _c64(out, "probe_out", (self.m, self.m)), _stream()))
+        return out
+
+    def probe_init_mean(self, amp, threshold=0.0):
+        out = torch.empty((self.m, self.m), dtype=torch.complex64, device=self.device)
+        _check(_C["sharp_probe_init_mean"](self.handle, _f32(amp, "amp", (self.K, self.m, self.m)),
+                                           float(threshold), _c64(out, "probe_out"), _stream()))
         return out
 
     def forward_amplitudes(self, obj, probe):

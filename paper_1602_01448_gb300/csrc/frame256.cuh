@@ -166,7 +166,7 @@ __device__ __forceinline__ void form_row(const FrameArgs& a, int py, int px, siz
                 for (int n = n0; n < n0 + CH; ++n)
                     st_hint(a.ebuf + fo + y * M + 16 * n + j, make_float2(-v[n].x, -v[n].y), pol_stream);
             }
-        } else if constexpr (MODE == MODE_PROJECT) {
+        } else if constexpr (MODE == MODE_PROJECT || MODE == MODE_MASK) {
 #pragma unroll
             for (int n = n0; n < n0 + CH; ++n) v[n] = ld_hint(a.zin + fo + y * M + 16 * n + j, pol_stream);
         } else {   // AMPS, LOSS, GRAD: z = w . obj(r + x_i)
@@ -194,6 +194,10 @@ __device__ __forceinline__ void fourier_col(const FrameArgs& a, size_t fo, int x
             const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
             a.amp_out[fo + (16 * q + j) * M + x] = m2 * rs * inv_m;
         }
+        return;
+    } else if constexpr (MODE == MODE_MASK) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = cscale(v[q], a.amp[fo + (16 * q + j) * M + x] * inv_m * inv_m);
         return;
     } else {
         float av[16];
@@ -242,7 +246,7 @@ __device__ __forceinline__ void finish_row(const FrameArgs& a, int py, int px, s
                 red_add_f2(a.accA + o, cmulc(wp[n - n0], v[n]));
                 if (a.write_e) red_hint(a.ebuf + fo + y * M + x, v[n], pol_stream);
             }
-        } else if constexpr (MODE == MODE_PROJECT) {
+        } else if constexpr (MODE == MODE_PROJECT || MODE == MODE_MASK) {
 #pragma unroll
             for (int n = n0; n < n0 + CH; ++n) st_hint(a.zout + fo + y * M + 16 * n + j, v[n], pol_stream);
         } else if constexpr (MODE == MODE_GRAD) {
@@ -304,7 +308,7 @@ __global__ void __launch_bounds__(NT, 1) big_kernel(const FrameArgs ap, const Ba
             if constexpr (MODE == MODE_RAAR) {
 #pragma unroll
                 for (int k = 0; k < 5; ++k) atomicAdd(a.sums + k, (double)s[k]);
-            } else if constexpr (MODE != MODE_AMPS) {
+            } else if constexpr (MODE != MODE_AMPS && MODE != MODE_MASK) {
                 atomicAdd(a.sums, (double)s[0]);
             }
         }

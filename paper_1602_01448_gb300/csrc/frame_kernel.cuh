@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a
         float2 v[32];
 
         // ------------------------------------------------ form the frame
-        if constexpr (MODE == MODE_PROJECT || MODE == MODE_PROJECT_PF) {
+        if constexpr (MODE == MODE_PROJECT || MODE == MODE_PROJECT_PF || MODE == MODE_MASK) {
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
                 const int y = q + TX * k;
@@ -100,6 +100,8 @@ __global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a
                 const float mag = m2 * rs * inv_m;     // |F z| on the unitary scale
                 if constexpr (MODE == MODE_AMPS) {
                     a.amp_out[fo + ky * M + kx] = mag;
+                } else if constexpr (MODE == MODE_MASK) {
+                    X = cscale(X, __ldg(ai + ky * M + kx) * inv_m * inv_m);
                 } else {
                     const float av = __ldg(ai + ky * M + kx);
                     const float d = av - mag;
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a
         G::inverse(v, S, tw);
 
         // ------------------------------------------------ epilogue
-        if constexpr (MODE == MODE_PROJECT || MODE == MODE_PROJECT_PF) {
+        if constexpr (MODE == MODE_PROJECT || MODE == MODE_PROJECT_PF || MODE == MODE_MASK) {
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
                 const int y = q + TX * k;
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, 1) frame_kernel(const FrameArgs a
         }
     }
 
-    if constexpr (MODE != MODE_PROJECT_PF) {
+    if constexpr (MODE != MODE_PROJECT_PF && MODE != MODE_MASK) {
         block_sum<NT, 5>(acc, red);
         if (tid == 0) {
             if constexpr (MODE != MODE_AMPS) atomicAdd(a.sums, (double)acc[0]);
@@ -175,6 +177,7 @@ cudaError_t launch_frames_m(int mode, int flags, const FrameArgs& a, cudaStream_
         case MODE_AMPS: return launch_one<M, MODE_AMPS, 0>(a, s);
         case MODE_LOSS: return launch_one<M, MODE_LOSS, 0>(a, s);
         case MODE_GRAD: return launch_one<M, MODE_GRAD, 0>(a, s);
+        case MODE_MASK: return launch_one<M, MODE_MASK, 0>(a, s);
         case MODE_RAAR: return launch_raar_m<M>(flags, a, s);
     }
     return cudaErrorInvalidValue;

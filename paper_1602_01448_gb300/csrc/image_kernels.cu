@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <cstring>
+
 #include "sharp_common.cuh"
 
 namespace sharp {
@@ -274,6 +276,137 @@ __global__ void metrics_final_kernel(const double* __restrict__ sums, double* __
     out[3] = na;
 }
 
+// ------------------------------------------------------------------ illumination refinement
+// Centre of mass of |w|^2 (Sec. 2.2 drift pathology): one block, FP64 sums of
+// |w|^2, row * |w|^2 and col * |w|^2 into out[0..2].
+__global__ void probe_moments_kernel(const float2* __restrict__ w, int m, double* __restrict__ out) {
+    __shared__ double sh[3][32];
+    double s0 = 0.0, sy = 0.0, sx = 0.0;
+    const int mm = m * m;
+    for (int l = threadIdx.x; l < mm; l += blockDim.x) {
+        const double v = (double)cabs2(w[l]);
+        s0 += v;
+        sy += v * (double)(l / m);
+        sx += v * (double)(l % m);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        sh[0][warp] = s0;
+        sh[1][warp] = sy;
+        sh[2][warp] = sx;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double t0 = lane < nw ? sh[0][lane] : 0.0, ty = lane < nw ? sh[1][lane] : 0.0,
+               tx = lane < nw ? sh[2][lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+            ty += __shfl_xor_sync(0xffffffffu, ty, o);
+            tx += __shfl_xor_sync(0xffffffffu, tx, o);
+        }
+        if (lane == 0) {
+            out[0] = t0;
+            out[1] = ty;
+            out[2] = tx;
+        }
+    }
+}
+
+// out(r) = in((r + d) mod m) with d = floor(centroid - m/2 + 1/2) per axis:
+// the roll that moves the centroid to the frame centre.  A zero probe is
+// copied unchanged.
+__global__ void probe_roll_kernel(const float2* __restrict__ in, float2* __restrict__ out, int m,
+                                  const double* __restrict__ mom) {
+    int dy = 0, dx = 0;
+    if (mom[0] > 0.0) {
+        dy = (int)floor(mom[1] / mom[0] - 0.5 * m + 0.5);
+        dx = (int)floor(mom[2] / mom[0] - 0.5 * m + 0.5);
+    }
+    dy = ((dy % m) + m) % m;
+    dx = ((dx % m) + m) % m;
+    const int mm = m * m;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < mm; l += gridDim.x * blockDim.x) {
+        int y = l / m + dy, x = l % m + dx;
+        y -= (y >= m) ? m : 0;
+        x -= (x >= m) ? m : 0;
+        out[l] = in[y * m + x];
+    }
+}
+
+// Mean intensity of the frames: acc[l] += sum over this block's chunk of
+// frames of amp^2 (FP64 atomics, one per pixel per chunk).
+__global__ void mean_frame_partial_kernel(const float* __restrict__ amp, int K, int mm, int chunk,
+                                          double* __restrict__ acc) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= mm) return;
+    const int f0 = blockIdx.y * chunk, f1 = min(K, f0 + chunk);
+    double s = 0.0;
+    for (int f = f0; f < f1; ++f) {
+        const float v = __ldcs(amp + (size_t)f * mm + l);
+        s += (double)v * v;
+    }
+    atomicAdd(acc + l, s);
+}
+
+// sqrt of the mean frame, or of its thresholded version (values below
+// t * max -> 0, the others -> their mean), into a_w; and the centred unit
+// impulse into z (its unitary transform has modulus 1/m and phase
+// (-1)^(qy+qx), so P_a of it with amplitudes a_w is the centred inverse
+// transform of a_w).  One block.
+__global__ void mean_frame_final_kernel(const double* __restrict__ acc, int K, int m, float threshold,
+                                        float* __restrict__ a_w, float2* __restrict__ z) {
+    __shared__ double sh[2][32];
+    const int mm = m * m;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double level = -1.0;   // < 0: no threshold
+    if (threshold > 0.f) {
+        double mx = 0.0;
+        for (int l = threadIdx.x; l < mm; l += blockDim.x) mx = fmax(mx, acc[l] / K);
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) sh[0][warp] = mx;
+        __syncthreads();
+        mx = 0.0;
+        for (int i = 0; i < nw; ++i) mx = fmax(mx, sh[0][i]);
+        __syncthreads();
+        const double thr = (double)threshold * mx;
+        double sum = 0.0, cnt = 0.0;
+        for (int l = threadIdx.x; l < mm; l += blockDim.x) {
+            const double v = acc[l] / K;
+            if (v >= thr) {
+                sum += v;
+                cnt += 1.0;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        }
+        if (lane == 0) {
+            sh[0][warp] = sum;
+            sh[1][warp] = cnt;
+        }
+        __syncthreads();
+        sum = 0.0;
+        cnt = 0.0;
+        for (int i = 0; i < nw; ++i) {
+            sum += sh[0][i];
+            cnt += sh[1][i];
+        }
+        level = cnt > 0.0 ? sum / cnt : 0.0;
+        for (int l = threadIdx.x; l < mm; l += blockDim.x)
+            a_w[l] = acc[l] / K >= thr ? (float)sqrt(level) : 0.f;
+    } else {
+        for (int l = threadIdx.x; l < mm; l += blockDim.x) a_w[l] = (float)sqrt(acc[l] / K);
+    }
+    const int c = (m / 2) * m + m / 2;
+    for (int l = threadIdx.x; l < mm; l += blockDim.x) z[l] = make_float2(l == c ? 1.f : 0.f, 0.f);
+}
+
 __global__ void copy_scaled_kernel(const double* src, double* dst, double scale) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *dst = *src * scale;
 }
@@ -449,6 +582,61 @@ cudaError_t launch_metrics_finalize(const Plan& p, double* metrics, int have_q, 
                                     cudaStream_t s) {
     metrics_final_kernel<<<1, 32, 0, s>>>(p.sums, metrics, have_q, have_d, delta_is_norm);
     return cudaGetLastError();
+}
+
+// Frame-kernel arguments for a single m x m "frame" (the probe).
+static FrameArgs probe_frame_args(const Plan& p, const float2* zin, float2* zout, const float* amp) {
+    FrameArgs a;
+    memset(&a, 0, sizeof(a));
+    a.K = 1;
+    a.m = p.m;
+    a.ny = p.ny;
+    a.nx = p.nx;
+    a.pos = p.pos;
+    a.zin = zin;
+    a.zout = zout;
+    a.amp = amp;
+    a.sums = p.scal + 16;   // residual slot of the single-frame launches
+    a.err = p.errflag;
+    a.counter = p.counter;
+    a.scratch = p.big_scratch;
+    return a;
+}
+
+cudaError_t launch_probe_refine(Plan& p, const float2* w_in, float2* w_out, cudaStream_t s) {
+    const int mm = p.m * p.m;
+    cudaError_t e = cudaSuccess;
+    const float2* cur = w_in;
+    if (p.probe_cons_kind != 0 && p.probe_cons) {
+        const int mode = p.probe_cons_kind == SHARP_PROBE_CONSTRAINT_MASK ? MODE_MASK : MODE_PROJECT;
+        e = launch_frames(mode, 0, probe_frame_args(p, cur, w_out, p.probe_cons), s);
+        if (e != cudaSuccess) return e;
+        cur = w_out;
+    }
+    if (p.probe_com) {
+        double* mom = p.scal + 20;
+        probe_moments_kernel<<<1, 1024, 0, s>>>(cur, p.m, mom);
+        probe_roll_kernel<<<grid_for(mm, 256), 256, 0, s>>>(cur, p.w_tmp, p.m, mom);
+        e = cudaMemcpyAsync(w_out, p.w_tmp, sizeof(float2) * mm, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+        cur = w_out;
+    }
+    if (cur != w_out) e = cudaMemcpyAsync(w_out, cur, sizeof(float2) * mm, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe_init_mean(Plan& p, const float* amp, float threshold, float2* w_out, cudaStream_t s) {
+    const int mm = p.m * p.m;
+    double* acc = p.probe_acc;   // first m*m doubles; not live outside a probe update
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * mm, s);
+    if (e != cudaSuccess) return e;
+    const int chunk = 64;
+    dim3 g((mm + 255) / 256, (p.K + chunk - 1) / chunk);
+    mean_frame_partial_kernel<<<g, 256, 0, s>>>(amp, p.K, mm, chunk, acc);
+    mean_frame_final_kernel<<<1, 1024, 0, s>>>(acc, p.K, p.m, threshold, p.w2tmp, p.w_tmp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_frames(MODE_PROJECT, 0, probe_frame_args(p, p.w_tmp, w_out, p.w2tmp), s);
 }
 
 cudaError_t launch_copy_scaled(const double* src, double* dst, double scale, cudaStream_t s) {

@@ -80,7 +80,7 @@ void free_plan(Plan& p) {
     void* ptrs[] = {p.pos,   p.tile_ptr,   p.tile_frames, p.w_cur, p.w_form,     p.w2,
                     p.Dsum,  p.invD,       p.dmax_bits,   p.accA,  p.accB,       p.ebuf,
                     p.sums,  p.probe_part, p.probe_acc,   p.scal,  p.w2tmp,      p.Dtmp,
-                    p.invDtmp, p.errflag, p.counter, p.big_scratch};
+                    p.invDtmp, p.errflag, p.counter, p.big_scratch, p.probe_cons, p.w_tmp};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     std::memset(&p, 0, sizeof(p));
@@ -191,6 +191,9 @@ int sharp::raar_step_finish(Plan& p, float2* state_c, float2* psi_y, float2* psi
     if (in.probe_due) {
         ck(timed_or_skip(K_PROBE, 3, [&] { return sharp::launch_probe_update_state(p, state_c, psi_y, psi, s); }),
            "probe update");
+        if (p.probe_com || (p.probe_cons_kind && p.probe_cons))
+            ck(timed_or_skip(K_PROBE, 2, [&] { return sharp::launch_probe_refine(p, p.w_cur, p.w_cur, s); }),
+               "probe refinement");
         ck(timed_or_skip(K_ILLUM, 3, [&] {
                return sharp::launch_illumination(p, p.w_cur, p.w2, p.Dsum, p.invD, p.dmax_bits, s);
            }), "illumination");
@@ -305,6 +308,7 @@ int sharp_plan_create(sharp_plan* out, int K, int m, int ny, int nx, const int32
     SHARP_ALLOC(invDtmp, n)
     SHARP_ALLOC(errflag, 1)
     SHARP_ALLOC(counter, 1)
+    SHARP_ALLOC(w_tmp, mm)
     if (m == 256) {   // one frame slab per SM for the line-pass transform
         int dev = 0, sms = 0;
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -428,6 +432,40 @@ int sharp_probe_update(sharp_plan plan, const float2* obj, const float2* z, cons
     SHARP_NONNULL(obj); SHARP_NONNULL(z); SHARP_NONNULL(probe_old); SHARP_NONNULL(probe_out);
     if (probe_out == probe_old) return fail(SHARP_ERR_INVALID_ARG, "probe_out must not alias probe_old");
     SHARP_CK(sharp::launch_probe_update_frames(plan->p, obj, z, probe_old, probe_out, s));
+    return SHARP_OK;
+}
+
+int sharp_plan_set_probe_refinement(sharp_plan plan, int constraint, const float* values, int center_of_mass,
+                                    cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    Plan& p = plan->p;
+    if (constraint < SHARP_PROBE_CONSTRAINT_NONE || constraint > SHARP_PROBE_CONSTRAINT_AMPLITUDE)
+        return fail(SHARP_ERR_INVALID_ARG, "unknown probe constraint %d", constraint);
+    if (constraint != SHARP_PROBE_CONSTRAINT_NONE && !values)
+        return fail(SHARP_ERR_INVALID_ARG, "the probe constraint needs its m x m values");
+    const size_t mm = (size_t)p.m * p.m;
+    if (constraint != SHARP_PROBE_CONSTRAINT_NONE) {
+        if (!p.probe_cons) SHARP_CK(dalloc(&p.probe_cons, mm));
+        SHARP_CK(cudaMemcpyAsync(p.probe_cons, values, mm * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    }
+    p.probe_cons_kind = constraint;
+    p.probe_com = center_of_mass ? 1 : 0;
+    return SHARP_OK;
+}
+
+int sharp_probe_refine(sharp_plan plan, const float2* probe_in, float2* probe_out, cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    SHARP_NONNULL(probe_in); SHARP_NONNULL(probe_out);
+    SHARP_CK(sharp::launch_probe_refine(plan->p, probe_in, probe_out, s));
+    return SHARP_OK;
+}
+
+int sharp_probe_init_mean(sharp_plan plan, const float* amp, float threshold, float2* probe_out, cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    SHARP_NONNULL(amp); SHARP_NONNULL(probe_out);
+    if (!(threshold >= 0.f && threshold <= 1.f))
+        return fail(SHARP_ERR_INVALID_ARG, "threshold = %g outside [0, 1]", threshold);
+    SHARP_CK(sharp::launch_probe_init_mean(plan->p, amp, threshold, probe_out, s));
     return SHARP_OK;
 }
 

@@ -208,7 +208,8 @@ int sharp_batch_step(sharp_batch b, int iter, cudaStream_t stream) {
             return r;
         const sharp::StepInfo& in = info[i];
         const uint64_t word = (uint64_t)(in.flags | in.have_q << 2 | in.have_d << 3 | in.delta_is_norm << 4 |
-                                         in.read_e << 5 | in.write_e << 6 | in.probe_due << 7 | fd << 8);
+                                         in.read_e << 5 | in.write_e << 6 | in.probe_due << 7 | fd << 8 |
+                                         p.probe_cons_kind << 9 | p.probe_com << 11);
         sig = (sig ^ word) * 1099511628211ull;
     }
     std::vector<int> gflags(b->groups.size(), 0);

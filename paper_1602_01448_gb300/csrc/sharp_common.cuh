@@ -114,13 +114,19 @@ struct Plan {
     int* errflag;            // device int: sticky error raised inside kernels
     int* counter;            // device int: work counter of the persistent frame pass
     float2* big_scratch;     // m = 256: one m*m slab per SM (frame transposition)
+    // illumination refinement after each probe update (Sec. 2.2, step 7)
+    float* probe_cons;       // m*m Fourier mask or Fourier amplitudes (nullptr = none)
+    int probe_cons_kind;     // SHARP_PROBE_CONSTRAINT_*
+    int probe_com;           // centre the probe after each update
+    float2* w_tmp;           // m*m scratch probe
 };
 
 constexpr int TILE = 32;
 
 // ------------------------------------------------ launchers (frame_kernels.cu)
 enum FrameMode { MODE_RAAR = 0, MODE_PROJECT = 1, MODE_AMPS = 2, MODE_LOSS = 3, MODE_GRAD = 4,
-                 MODE_PROJECT_PF = 5 /* P_a with one residual per frame in sums[i] */ };
+                 MODE_PROJECT_PF = 5 /* P_a with one residual per frame in sums[i] */,
+                 MODE_MASK = 6 /* F^-1{(F z) mask}, mask in `amp` */ };
 
 struct FrameArgs {
     int K, m, ny, nx, wrap;
@@ -203,6 +209,11 @@ cudaError_t launch_metrics_finalize(const Plan& p, double* metrics, int have_q, 
 cudaError_t launch_solution_error(Plan& p, const float2* psi, const float2* psi_true, const float2* probe,
                                   double* out, cudaStream_t s);
 cudaError_t launch_copy_scaled(const double* src, double* dst, double scale, cudaStream_t s);
+// Fourier constraint (if configured) then centring (if configured) of probe
+// w_in -> w_out (may alias), Sec. 2.2 step 7.
+cudaError_t launch_probe_refine(Plan& p, const float2* w_in, float2* w_out, cudaStream_t s);
+// Initial illumination from the mean frame of amp (Sec. 2.2 step 2, Sec. 4).
+cudaError_t launch_probe_init_mean(Plan& p, const float* amp, float threshold, float2* w_out, cudaStream_t s);
 
 // Message returned by sharp_last_error() on this thread (sharp_api.cu).
 void set_last_error(const char* msg);
