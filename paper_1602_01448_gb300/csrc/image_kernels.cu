@@ -43,11 +43,14 @@ __global__ void w2_kernel(const float2* __restrict__ w, float* __restrict__ w2, 
 
 // Frame list entries of a tile staged in shared memory per round.
 constexpr int GATHER_STAGE = 512;
+// Frames summed in plain FP32 before each compensated (Kahan) add.
+constexpr int GATHER_GROUP = 16;
 
+template <int WRAP>
 __global__ void __launch_bounds__(GATHER_THREADS)
 illum_gather_kernel(const int32_t* __restrict__ pos, const int* __restrict__ tptr,
                     const int* __restrict__ tfr, const float* __restrict__ w2, float* __restrict__ D,
-                    unsigned* __restrict__ dmax_bits, int m, int ny, int nx, int tiles_x, int wrap) {
+                    unsigned* __restrict__ dmax_bits, int m, int ny, int nx, int tiles_x) {
     __shared__ int2 sp[GATHER_STAGE];          // (row, col) of the staged frames
     const int tile = blockIdx.x;
     const int gx = (tile % tiles_x) * TILE + (threadIdx.x & 31);
@@ -62,17 +65,26 @@ illum_gather_kernel(const int32_t* __restrict__ pos, const int* __restrict__ tpt
             sp[t] = make_int2(__ldg(pos + 2 * f), __ldg(pos + 2 * f + 1));
         }
         __syncthreads();
+        for (int t0 = 0; t0 < n; t0 += GATHER_GROUP) {
+            const int t1 = min(n, t0 + GATHER_GROUP);
+            float part[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
-        for (int t = 0; t < n; ++t) {
-            const int2 p = sp[t];
-            const int lx = local_offset(gx, p.y, nx, wrap, m);
-            if (lx >= m) continue;             // this column is outside the frame
-            const float* wr = w2 + lx;
+            for (int t = t0; t < t1; ++t) {
+                const int2 p = sp[t];
+                int lx = gx - p.y;
+                if (WRAP && lx < 0) lx += nx;
+                if ((unsigned)lx >= (unsigned)m) continue;   // column outside this frame
+                const float* wr = w2 + lx;
+                const int ly0 = gy0 - p.x;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int ly = local_offset(gy0 + 8 * r, p.x, ny, wrap, m);
-                if (ly < m) kahan_add(s[r], cc[r], __ldg(wr + ly * m));
+                for (int r = 0; r < 4; ++r) {
+                    int ly = ly0 + 8 * r;
+                    if (WRAP && ly < 0) ly += ny;
+                    if ((unsigned)ly < (unsigned)m) part[r] += __ldg(wr + ly * m);
+                }
             }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) kahan_add(s[r], cc[r], part[r]);
         }
     }
     float mx = 0.f;
@@ -188,7 +200,7 @@ __global__ void probe_partial_kernel(const int32_t* __restrict__ pos, const floa
                                      const float2* __restrict__ zc, const float2* __restrict__ psiy,
                                      const float2* __restrict__ w, float* __restrict__ part, int K, int m,
                                      int ny, int nx, int wrap) {
-    constexpr int U = 4;   // frames in flight per thread
+    constexpr int U = 8;   // frames in flight per thread
     const int mm = m * m;
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= mm) return;
@@ -203,7 +215,7 @@ __global__ void probe_partial_kernel(const int32_t* __restrict__ pos, const floa
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int g = min(f + u, f1 - 1);
-            const int o = obj_index(pos[2 * g], pos[2 * g + 1], y, x, ny, nx, wrap);
+            const int o = obj_index(__ldg(pos + 2 * g), __ldg(pos + 2 * g + 1), y, x, ny, nx, wrap);
             ps[u] = __ldg(psi + o);
             zz[u] = __ldcs(zc + (size_t)g * mm + l);
             yy[u] = psiy ? __ldg(psiy + o) : make_float2(0.f, 0.f);
@@ -224,31 +236,43 @@ __global__ void probe_partial_kernel(const int32_t* __restrict__ pos, const floa
     pc[2 * mm + l] = dn;
 }
 
-__global__ void probe_reduce_kernel(const float* __restrict__ part, double* __restrict__ acc, int chunks,
-                                    int mm, unsigned long long* __restrict__ dmax) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+// FP64 sum over chunks of the FP32 partials: 32 probe pixels per block, the
+// chunks split over the block's 8 warps, then combined in a fixed order; the
+// largest denominator goes to dmax (as ordered bits: it is >= 0).
+__global__ void __launch_bounds__(256) probe_reduce_kernel(const float* __restrict__ part, double* __restrict__ acc,
+                                                           int chunks, int mm, unsigned long long* __restrict__ dmax) {
+    __shared__ double sh[3][8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int l = blockIdx.x * 32 + lane;
     double nr = 0.0, ni = 0.0, dn = 0.0;
     if (l < mm) {
-        for (int c = 0; c < chunks; ++c) {
+        for (int c = warp; c < chunks; c += 8) {
             const float* pc = part + (size_t)c * 3 * mm;
             nr += pc[l];
             ni += pc[mm + l];
             dn += pc[2 * mm + l];
         }
-        acc[l] = nr;
-        acc[mm + l] = ni;
-        acc[2 * mm + l] = dn;
     }
-    // dn >= 0, so its bit pattern orders like the value
-    unsigned long long bits = (unsigned long long)__double_as_longlong(dn);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
-        bits = ob > bits ? ob : bits;
+    sh[0][warp][lane] = nr;
+    sh[1][warp][lane] = ni;
+    sh[2][warp][lane] = dn;
+    __syncthreads();
+    if (warp < 3) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += sh[warp][k][lane];
+        if (l < mm) acc[warp * mm + l] = t;
+        if (warp == 2) {
+            unsigned long long bits = (unsigned long long)__double_as_longlong(l < mm ? t : 0.0);
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+                bits = ob > bits ? ob : bits;
+            }
+            if (lane == 0) atomicMax(dmax, bits);
+        }
     }
-    if ((threadIdx.x & 31) == 0) atomicMax(dmax, bits);
 }
 
+// w_new = num / den, or w_old where den <= 1e-12 of the largest (reading R6).
 __global__ void probe_final_kernel(const double* __restrict__ acc, const float2* __restrict__ w_old,
                                    float2* __restrict__ w_new, int mm,
                                    const unsigned long long* __restrict__ dmax) {
@@ -256,11 +280,7 @@ __global__ void probe_final_kernel(const double* __restrict__ acc, const float2*
     if (l >= mm) return;
     const double thr = 1e-12 * __longlong_as_double((long long)*dmax);
     const double dn = acc[2 * mm + l];
-    if (dn > thr) {
-        w_new[l] = make_float2((float)(acc[l] / dn), (float)(acc[mm + l] / dn));
-    } else {
-        w_new[l] = w_old[l];
-    }
+    w_new[l] = dn > thr ? make_float2((float)(acc[l] / dn), (float)(acc[mm + l] / dn)) : w_old[l];
 }
 
 // ------------------------------------------------------------------ metrics
@@ -281,14 +301,17 @@ __global__ void metrics_final_kernel(const double* __restrict__ sums, double* __
 // |w|^2, row * |w|^2 and col * |w|^2 into out[0..2].
 __global__ void probe_moments_kernel(const float2* __restrict__ w, int m, double* __restrict__ out) {
     __shared__ double sh[3][32];
-    double s0 = 0.0, sy = 0.0, sx = 0.0;
+    // FP32 per thread (a few dozen terms), FP64 across threads (GB300's FP64
+    // rate is low, so the per-element work stays in FP32)
+    float f0 = 0.f, fy = 0.f, fx = 0.f;
     const int mm = m * m;
     for (int l = threadIdx.x; l < mm; l += blockDim.x) {
-        const double v = (double)cabs2(w[l]);
-        s0 += v;
-        sy += v * (double)(l / m);
-        sx += v * (double)(l % m);
+        const float v = cabs2(w[l]);
+        f0 += v;
+        fy = fmaf(v, (float)(l / m), fy);
+        fx = fmaf(v, (float)(l % m), fx);
     }
+    double s0 = f0, sy = fy, sx = fx;
     for (int o = 16; o > 0; o >>= 1) {
         s0 += __shfl_xor_sync(0xffffffffu, s0, o);
         sy += __shfl_xor_sync(0xffffffffu, sy, o);
@@ -508,8 +531,12 @@ static cudaError_t illum_for(const Plan& p, const float2* w, float* w2, float* D
     w2_kernel<<<grid_for(mm, 256), 256, 0, s>>>(w, w2, mm);
     cudaError_t e = cudaMemsetAsync(dmax, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    illum_gather_kernel<<<p.tiles_y * p.tiles_x, GATHER_THREADS, 0, s>>>(
-        p.pos, p.tile_ptr, p.tile_frames, w2, D, dmax, p.m, p.ny, p.nx, p.tiles_x, p.prm.wrap);
+    if (p.prm.wrap)
+        illum_gather_kernel<1><<<p.tiles_y * p.tiles_x, GATHER_THREADS, 0, s>>>(
+            p.pos, p.tile_ptr, p.tile_frames, w2, D, dmax, p.m, p.ny, p.nx, p.tiles_x);
+    else
+        illum_gather_kernel<0><<<p.tiles_y * p.tiles_x, GATHER_THREADS, 0, s>>>(
+            p.pos, p.tile_ptr, p.tile_frames, w2, D, dmax, p.m, p.ny, p.nx, p.tiles_x);
     return cudaGetLastError();
 }
 
@@ -558,7 +585,7 @@ static cudaError_t probe_common(Plan& p, const float2* psi, const float2* zc, co
     unsigned long long* dmax = reinterpret_cast<unsigned long long*>(p.scal);
     cudaError_t e = cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    probe_reduce_kernel<<<(mm + 255) / 256, 256, 0, s>>>(p.probe_part, p.probe_acc, p.probe_chunks, mm, dmax);
+    probe_reduce_kernel<<<(mm + 31) / 32, 256, 0, s>>>(p.probe_part, p.probe_acc, p.probe_chunks, mm, dmax);
     probe_final_kernel<<<(mm + 255) / 256, 256, 0, s>>>(p.probe_acc, w_old, w_out, mm, dmax);
     return cudaGetLastError();
 }

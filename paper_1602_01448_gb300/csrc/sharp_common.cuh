@@ -101,9 +101,9 @@ struct Plan {
     int last_iter;           // last step run (0 = none)
     // reductions
     double* sums;            // 16 doubles of per-step sums
-    float* probe_part;       // partial sums of the probe update (chunks x 3 x m*m)
     int probe_chunks;
-    double* probe_acc;       // 3 x m*m doubles
+    float* probe_part;       // FP32 partial sums of Eq. 10 per chunk of frames (chunks x 3 x m*m)
+    double* probe_acc;       // 3 x m*m doubles (FP64 sums over the chunks)
     double* scal;            // 32 doubles of misc scalars
     // scratch for operations on a caller-given probe (standalone operators)
     float* w2tmp;            // m*m
