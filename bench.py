@@ -5,7 +5,7 @@ an end-to-end figure through the C ABI with host buffers, and the FP64 oracle
 timed on the host cores as a reported CPU baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload fermat|raster256]
+                  [--workload fermat|raster256|batch]
 
 --workload raster256 times the large scan instead: a 100 x 100 raster of
 256^2 frames (step 24 +-1 px) over a 3072^2 object, Poisson 10^8 photons,
@@ -386,6 +386,120 @@ def run_ours(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def batch_scans(n_scans: int = 32, seed: int = 7):
+    """32 independent scans: frame size drawn from {64, 128, 256}, frame count
+    uniform in [100, 4000]; each a raster of side ceil(sqrt(K)) with step
+    round(0.1875 m), object = scan extent + 64 px, Poisson 10^U[5,7]."""
+    import synth
+    rng = np.random.default_rng(seed)
+    ms = rng.choice([64, 128, 256], size=n_scans)
+    ks = rng.integers(100, 4001, size=n_scans)
+    return [synth.scan_batch_member(100 + i, int(m), int(k)) for i, (m, k) in enumerate(zip(ms, ks))]
+
+
+def run_batch(args, rank, world):
+    """Batched multi-scan RAAR: every step runs one persistent frame pass per
+    frame size over all scans (sharp_batch_step, replayed as a CUDA graph);
+    compared with stepping the same scans one after another."""
+    import torch
+    import paper_1602_01448_gb300 as S
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scans = batch_scans()
+    total = sum(sc.K for sc in scans)
+    alg_bytes = sum(20.0 * sc.m * sc.m * sc.K for sc in scans)
+
+    def make(sc, amp=None):
+        plan = S.Plan(sc.pos, sc.m, sc.shape, beta=0.75, residual_every=RESIDUAL_EVERY, device=dev)
+        if amp is None:
+            a = plan.forward_amplitudes(torch.as_tensor(sc.obj).to(torch.complex64).to(dev),
+                                        torch.as_tensor(sc.probe).to(torch.complex64).to(dev))
+            amp = device_poisson(a, sc.photons, sc.seed)
+        plan.raar_init(torch.as_tensor(sc.psi_init).to(torch.complex64).to(dev),
+                       torch.as_tensor(sc.probe_init).to(torch.complex64).to(dev))
+        return plan, amp
+
+    made = [make(sc) for sc in scans]
+    plans, amps = [p for p, _ in made], [a for _, a in made]
+    batch = S.Batch(plans, amps)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(max(args.warmup, 4)):        # includes the grid autotuning steps
+        batch.step()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ms_total = timed(batch.step, args.steps)
+    clocks = sampler.stop()
+    batch.status()
+    ms_total = slowest_rank_ms(ms_total, world, dev)
+    ms_step = ms_total / args.steps
+
+    # the same scans stepped one after another through sharp_raar_step
+    singles = [make(sc, a)[0] for sc, a in zip(scans, amps)]
+
+    def one_by_one():
+        for p, a in zip(singles, amps):
+            p.raar_step(a)
+
+    for _ in range(args.warmup):
+        one_by_one()
+    ms_single = timed(one_by_one, args.steps) / args.steps
+    if rank != 0:
+        return
+    grids = {m: batch.tuned_grid(m) for m in (64, 128, 256)}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        import synth
+        sc = scans[0]
+        n = min(sc.K, 300)
+        inten = O.forward_amplitudes(sc.obj, sc.probe, sc.pos[:n]) ** 2
+        a_o = np.sqrt(synth.poisson_intensities(inten, sc.photons, 5))
+        rate, dt = oracle_sample_rate(sc, a_o, n, 1)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one FP64 RAAR step + object update over {n} frames of {sc.m}^2 "
+                         f"(first scan of the batch), {dt:.1f} s, NumPy single thread"}
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg_bytes / (ms_step / 1000.0) / 1e9
+    out = {
+        "metric": METRIC, "value": world * total * args.steps / (ms_total / 1000.0), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"batch-{len(scans)}scans-{total}frames", "scans": len(scans), "frames": total,
+                   "frames_by_size": {str(m): sum(sc.K for sc in scans if sc.m == m) for m in (64, 128, 256)},
+                   "beta": 0.75, "probe_every": 0, "residual_every": RESIDUAL_EVERY,
+                   "parallelism": f"replicas{world}", "tuned_grid": grids,
+                   "l2": f"inputs larger than L2 ({alg_bytes * 0.6 / 1e9:.1f} GB of state + amplitudes read per step)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "whole step (all launches of sharp_batch_step)",
+                     "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes, "kernel_ms": ms_step},
+        "one_by_one": {"ms_per_step": ms_single, "value": total / (ms_single / 1000.0),
+                       "speedup_of_batch": ms_single / ms_step},
+        "cpu_baseline": cpu,
+        "e2e": None,
+        # per step: one frame pass per frame size, then per scan the image
+        # pass and the metric finalisation (no probe updates in this workload)
+        "gpu_launches": args.steps * (len({sc.m for sc in scans}) + 2 * len(scans)),
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,7 +507,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="fermat", choices=["fermat", "raster256"])
+    ap.add_argument("--workload", default="fermat", choices=["fermat", "raster256", "batch"])
     ap.add_argument("--frames", type=int, default=None,
                     help="frames of the scan (default: the workload's; fewer for small ncu captures; "
                          "raster256 rounds to a square raster)")
@@ -407,7 +521,10 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl")
-    run_ours(args, rank, world)
+    if args.workload == "batch":
+        run_batch(args, rank, world)
+    else:
+        run_ours(args, rank, world)
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()
