@@ -105,6 +105,48 @@ def test_residual_cadence_and_nan_off_cadence():
             assert np.isnan(met[1]) and np.isnan(met[2])
 
 
+@pytest.mark.parametrize("beta", [1.0, 0.55])
+def test_raar_beta_extremes_match_oracle(beta):
+    # beta = 1 is Douglas-Rachford (2 P_Q P_a - P_Q - P_a + I); beta near 1/2
+    # makes 1/(1-2b) in the image pass large
+    S = _lib()
+    obj, w, pos, shape, a = _noisy_scan(64, 4, 12, 21, seed=13)
+    psi0 = synth.random_object(shape, np.random.default_rng(14), phase_sigma=1.0)
+    ref = O.raar_reconstruct(a, pos, shape, w, psi0, 3, beta=beta)
+    plan = S.Plan(pos, 64, shape, beta=beta, residual_every=1)
+    plan.raar_init(dev(psi0), dev(w))
+    ta = dev(a, torch.float32)
+    for step_i in range(3):
+        met = host(plan.raar_step(ta)).real
+        _check_metrics(met, ref["history"][step_i], step_i == 0)
+    D = O.illumination(w, pos, shape)
+    vis = D > 1e-3 * D.max()
+    assert rel_l2(host(plan.psi), ref["psi"], vis) < 1e-4 * (1 + 4 * (beta < 0.6))
+
+
+def test_single_frame_scan_matches_oracle():
+    S = _lib()
+    m = 128
+    rng = np.random.default_rng(15)
+    shape = (m + 9, m + 3)
+    obj = synth.random_object(shape, rng)
+    w = synth.gaussian_probe(m, m / 6.0, rng)
+    pos = np.array([[5, 2]], np.int32)
+    a = O.forward_amplitudes(obj, w, pos) * (1 + 0.1 * rng.standard_normal((1, m, m)))
+    a = np.abs(a).astype(np.float32).astype(np.float64)
+    psi0 = synth.random_object(shape, rng, phase_sigma=1.0)
+    ref = O.raar_reconstruct(a, pos, shape, w, psi0, 3)
+    plan = S.Plan(pos, m, shape, residual_every=1)
+    plan.raar_init(dev(psi0), dev(w))
+    for step_i in range(3):
+        met = host(plan.raar_step(dev(a, torch.float32))).real
+        _check_metrics(met, ref["history"][step_i], step_i == 0)
+    D = O.illumination(w, pos, shape)
+    vis = D > 1e-3 * D.max()
+    assert rel_l2(host(plan.psi), ref["psi"], vis) < 3e-5
+    assert np.all(host(plan.psi)[~(D > 1e-12 * D.max())] == 0)
+
+
 def test_exact_data_is_a_fixed_point_on_gpu():
     S = _lib()
     obj, w, pos, shape, a = _noisy_scan(64, 5, 12, 16, seed=5, photons=None)
@@ -151,19 +193,27 @@ def test_small_raster_nrmse_within_2_percent_of_oracle():
     print("eps_0 ratio GPU/oracle by iteration:", {k: round(v, 4) for k, v in ratios.items()})
 
 
-def test_full_size_fermat_step_on_sampled_outputs():
-    # The 2500-frame 128^2 Fermat scan over a 1024^2 object, one fused step in
-    # the launch configuration the benchmark times; checked on sampled frames
-    # (c update) and a sampled image patch (object update) that the oracle
-    # computes frame by frame.
+def _host_amplitudes(s, seed, chunk=500):
+    """Amplitudes of the scan from the oracle's forward model (Eq. 1), with
+    5 % multiplicative noise, computed on the host in chunks of frames."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((s.K, s.m, s.m), np.float32)
+    for k0 in range(0, s.K, chunk):
+        a = O.forward_amplitudes(s.obj, s.probe, s.pos[k0:k0 + chunk], s.wrap)
+        out[k0:k0 + chunk] = np.abs(a * (1.0 + 0.05 * rng.standard_normal(a.shape)))
+    return out
+
+
+def _sampled_step_parity(s, patch, beta=0.75, n_frames=6):
+    """One fused RAAR step of a full-size scan, in the launch configuration the
+    benchmark times, checked on sampled frames (state update) and on a small
+    image patch (object update) that the oracle computes frame by frame."""
     S = _lib()
-    s = synth.scan_fermat()
     m, K = s.m, s.K
     rng = np.random.default_rng(0)
-    plan = S.Plan(s.pos, m, s.shape, beta=0.75, residual_every=1)
-    amp = plan.forward_amplitudes(dev(s.obj), dev(s.probe))
-    amp.mul_(1.0 + 0.05 * torch.randn(amp.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(1)))
-    amp.abs_()
+    a_h = _host_amplitudes(s, 1)
+    plan = S.Plan(s.pos, m, s.shape, beta=beta, wrap=s.wrap, residual_every=1)
+    amp = dev(a_h, torch.float32)
     plan.raar_init(dev(s.psi_init), dev(s.probe_init))
     # run one step so that c != 0, then snapshot the inputs of the checked step
     plan.raar_step(amp)
@@ -171,26 +221,24 @@ def test_full_size_fermat_step_on_sampled_outputs():
     psiy_in = host(plan.psi_y)
     plan.raar_step(amp)
     w = s.probe_init
-    frames = rng.choice(K, 6, replace=False)
-    a_h = host(amp).real
-    c_in_h = {int(i): host(c_in[int(i)]) for i in frames}
-    for i in frames:
+    a_h = a_h.astype(np.float64)
+    for i in rng.choice(K, n_frames, replace=False):
         i = int(i)
-        z = O.split(psiy_in, w, s.pos[i:i + 1])[0] + c_in_h[i]
+        z = O.split(psiy_in, w, s.pos[i:i + 1], s.wrap)[0] + host(c_in[i])
         p = O.data_project(z[None], a_h[i][None])[0]
-        c_ref = (1 - 1.5) * p + 0.75 * z
-        assert rel_l2(host(plan.c[i]), c_ref) < 1e-5
-    # object on a 6x6 patch near the scan centre: A = sum conj(w) P_a z over
-    # every frame touching the patch
-    y0, x0, P = 500, 520, 6
+        c_ref = (1 - 2 * beta) * p + beta * z
+        assert rel_l2(host(plan.c[i]), c_ref) < 1e-5, i
+    # object on a small patch away from the object edges: A = sum conj(w) P_a z
+    # over every frame touching the patch
+    y0, x0, P = patch
     cover = [i for i in range(K) if s.pos[i, 0] < y0 + P and y0 < s.pos[i, 0] + m
              and s.pos[i, 1] < x0 + P and x0 < s.pos[i, 1] + m]
-    assert len(cover) > 50
+    assert len(cover) > 20
     c_all = host(c_in[torch.tensor(cover, device="cuda")])
     A = np.zeros((P, P), complex)
     Dp = np.zeros((P, P))
     for j, i in enumerate(cover):
-        z = O.split(psiy_in, w, s.pos[i:i + 1])[0] + c_all[j]
+        z = O.split(psiy_in, w, s.pos[i:i + 1], s.wrap)[0] + c_all[j]
         p = O.data_project(z[None], a_h[i][None])[0]
         ya, yb = max(y0, s.pos[i, 0]), min(y0 + P, s.pos[i, 0] + m)
         xa, xb = max(x0, s.pos[i, 1]), min(x0 + P, s.pos[i, 1] + m)
@@ -198,6 +246,21 @@ def test_full_size_fermat_step_on_sampled_outputs():
         sl = (slice(ly, ly + yb - ya), slice(lx, lx + xb - xa))
         A[ya - y0:yb - y0, xa - x0:xb - x0] += np.conj(w[sl]) * p[sl]
         Dp[ya - y0:yb - y0, xa - x0:xb - x0] += np.abs(w[sl]) ** 2
-    D_full = O.illumination(w, s.pos, s.shape)[y0:y0 + P, x0:x0 + P]
+    D_full = O.illumination(w, s.pos, s.shape, s.wrap)[y0:y0 + P, x0:x0 + P]
     np.testing.assert_allclose(Dp, D_full, rtol=1e-12)
     assert rel_l2(host(plan.psi)[y0:y0 + P, x0:x0 + P], A / Dp) < 1e-5
+
+
+def test_full_size_fermat_step_on_sampled_outputs():
+    # 2500 frames of 128^2 on a Fermat spiral over a 1024^2 object
+    _sampled_step_parity(synth.scan_fermat(), (500, 520, 6))
+
+
+def test_full_size_large_raster_step_on_sampled_outputs():
+    # 10^4 frames of 256^2 on a 100 x 100 raster over a 3072^2 object
+    _sampled_step_parity(synth.scan_large_raster(), (1500, 1490, 6))
+
+
+def test_full_size_wrapped_raster_step_on_sampled_outputs():
+    # 1600 frames of 128^2 on a 40 x 40 raster over a periodic 512^2 object
+    _sampled_step_parity(synth.scan_wrapped_raster(), (250, 260, 6))
