@@ -21,6 +21,7 @@ __all__ = [
     "sharp_solution_error", "sharp_forward_amplitudes", "sharp_amp_loss",
     "sharp_amp_loss_backward", "AmpLoss", "amp_loss", "sharp_plan_set_profiling",
     "sharp_plan_kernel_times", "sharp_plan_status", "sharp_fourier_project_noalloc", "Batch",
+    "SHARP_PROBE_CONSTRAINT_NONE", "SHARP_PROBE_CONSTRAINT_MASK", "SHARP_PROBE_CONSTRAINT_AMPLITUDE",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

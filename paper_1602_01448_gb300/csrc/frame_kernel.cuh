@@ -1,20 +1,17 @@
 // Per-frame kernels for the standalone operators: one thread block transforms
-// one m x m frame in registers and shared memory (fft_frame.cuh).  Modes: the
-// data projection P_a (Eq. 7) of explicit frames, the forward model (Eq. 1),
-// the amplitude loss and its adjoint.  The fused RAAR step lives in
-// raar_kernel.cuh.  (Earlier design notes, kept for the algebra:) for frame i,
-//   z_i = w_f . psi_y(r + x_i) + c_i                  (implicit iterate, split Q: Sec. 2.1)
-//   Z = F z_i;  Z' = a_i Z/|Z|;  p_i = F* Z'           (P_a, Eq. 7)
-//   R_A(r + x_i) += conj(w) (p_i - w rho)  [R_B += conj(w) (z_i - w rho)]   (Q*, Eqs. 8-9)
-//   c_i <- (1 - 2b) p_i + b z_i                          (RAAR state, Sec. 2.2)
-// plus the residual partial sums of Eqs. 11-13.  With P_Q y = Q (Q*y / Q*Q)
-// the Luke-form update z+ = P_Q(2b P_a z - b z) + (1-2b) P_a z + b z becomes
-// z+ = w . psi_y + c with psi_y = (2b A - b B)/D, which the image pass forms
-// from A = Q* P_a z and B = Q* z; and Q* z+ = A, so B/D of the next step is
-// this step's object A/D.  The overlap sums are accumulated relative to the
-// reference image rho = psi_y / b (A = D rho + R_A), which tends to the object
-// itself: near convergence the FP32 sums then hold only small corrections and
-// their rounding no longer sets the error floor of the object.
+// one m x m frame in registers and shared memory (fft_frame.cuh), one block
+// per frame.  Modes:
+//   MODE_PROJECT    P_a z = F* (a Fz/|Fz|) of explicit frames (Eq. 7) and the
+//                   residual sum ||P_a z - z||^2
+//   MODE_PROJECT_PF the same with one residual per frame (allocation-free entry)
+//   MODE_AMPS       forward model a = |F (w . obj(r + x_i))| (Eq. 1)
+//   MODE_LOSS       sum (|F z| - a)^2 with z = w . obj(r + x_i)
+//   MODE_GRAD       adjoint of the loss: r = z - P_a z scattered as conj(w) r
+//                   (object) and conj(obj) r (probe)
+//   MODE_MASK       F^-1{(F z) mask} (the illumination Fourier-mask constraint,
+//                   Sec. 2.2 step 7)
+// The fused RAAR step lives in raar_kernel.cuh (64^2, 128^2) and frame256.cuh
+// (256^2, which also serves these modes for 256^2 frames).
 #pragma once
 #include <cuda_runtime.h>
 
