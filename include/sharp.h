@@ -42,7 +42,7 @@ extern "C" {
 
 #define SHARP_OK                   0
 #define SHARP_ERR_INVALID_ARG      1  /* null pointer, bad size, position out of range, ... */
-#define SHARP_ERR_UNSUPPORTED_SIZE 2  /* frame size without a kernel (m not in {64,128}) */
+#define SHARP_ERR_UNSUPPORTED_SIZE 2  /* frame size without a kernel (m not in {64,128,256}) */
 #define SHARP_ERR_CUDA             3  /* a CUDA runtime call or launch failed */
 #define SHARP_ERR_TIMEOUT          4  /* a bounded device-side wait gave up */
 #define SHARP_ERR_STATE            5  /* call order violated (e.g. step before init) */
@@ -78,7 +78,8 @@ void sharp_default_params(sharp_params* p);
  *            wrap positions are reduced modulo (ny, nx).
  *   params : copied; NULL means sharp_default_params().
  * Allocates the plan's scratch (illumination sum, overlap accumulators,
- * per-tile frame lists, reduction buffers).  The per-block lists of frames
+ * per-tile frame lists, reduction buffers; for m = 256 also one m x m
+ * transposition slab per SM, 78 MB on 152 SMs).  The per-block lists of frames
  * that touch each image block (Sec. 2.3) are built here once, on the host.
  * Errors: INVALID_ARG (K < 1, ny or nx < m, bad position), UNSUPPORTED_SIZE.
  */
@@ -150,7 +151,7 @@ int sharp_probe_refine(sharp_plan plan, const float2* probe_in, float2* probe_ou
 
 /*
  * Initial illumination from the average frame (Sec. 2.2 reconstruction
- * sequence step 2; threshold variant of Sec. 4):
+ * sequence step 2; threshold variant of Sec. 3.2):
  *   I(q)   = (1/K) sum_i amp_i(q)^2                (amplitudes on the unitary scale)
  *   I'(q)  = I(q), or with 0 < threshold <= 1: 0 where I < threshold * max I and
  *            the mean of the remaining values elsewhere
@@ -229,7 +230,7 @@ int sharp_amp_loss_backward(sharp_plan plan, const float2* obj, const float2* pr
 
 /*
  * Batched RAAR: independent scans (the multi-scan workloads of a streaming
- * beamline, Sec. 3) stepped together.  Each scan keeps its own plan, state,
+ * beamline, Sec. 3.3) stepped together.  Each scan keeps its own plan, state,
  * amplitudes and probe; every sharp_batch_step(iter) performs one RAAR step
  * (as sharp_raar_step) for every scan with one persistent frame-pass launch
  * per frame size over the frames of all scans of that size, then each scan's

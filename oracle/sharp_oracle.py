@@ -38,7 +38,7 @@ Readings of the paper taken here (each also listed in the design notes):
   R13 Illumination Fourier constraints (sequence step 7): F is the unitary
       transform of Eq. 2; a mask multiplies Fw, amplitudes a_w replace |Fw|
       (phase 1 where Fw = 0, as R3).  Order: Eq. 10, constraint, centring.
-  R14 Initial illumination (sequence step 2; Sec. 4 variant): the average
+  R14 Initial illumination (sequence step 2; Sec. 3.2 variant): the average
       frame is the mean over frames of a_i^2 on the unitary scale; its
       square root is inverse-transformed and centred in the frame (rolled
       by m/2, i.e. the spectrum multiplied by (-1)^(qy+qx)).  With a
@@ -278,7 +278,7 @@ def forward_amplitudes(psi, w, pos, wrap=False):
 # --------------------------------------------------------------------------
 # --------------------------------------------------------------------------
 # Sec. 2.2 -- illumination pathologies and initialisation (reconstruction
-# sequence steps 2 and 7; the threshold variant of Sec. 4)
+# sequence steps 2 and 7; the threshold variant of Sec. 3.2)
 # --------------------------------------------------------------------------
 def probe_centroid(w):
     """Centre of mass (row, col) of |w|^2 over frame indices 0..m-1 (R12)."""
@@ -317,7 +317,7 @@ def probe_fourier_amplitude(w, a_w):
 
 def probe_from_mean_frame(a, threshold=0.0):
     """Initial illumination from the average frame (sequence step 2; with a
-    threshold, the variant of Sec. 4), centred in the frame (R14)."""
+    threshold, the variant of Sec. 3.2), centred in the frame (R14)."""
     a = np.asarray(a, dtype=np.float64)
     m = a.shape[-1]
     mean = np.mean(a ** 2, axis=0)

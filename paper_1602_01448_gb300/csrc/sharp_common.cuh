@@ -212,7 +212,7 @@ cudaError_t launch_copy_scaled(const double* src, double* dst, double scale, cud
 // Fourier constraint (if configured) then centring (if configured) of probe
 // w_in -> w_out (may alias), Sec. 2.2 step 7.
 cudaError_t launch_probe_refine(Plan& p, const float2* w_in, float2* w_out, cudaStream_t s);
-// Initial illumination from the mean frame of amp (Sec. 2.2 step 2, Sec. 4).
+// Initial illumination from the mean frame of amp (Sec. 2.2 step 2, Sec. 3.2).
 cudaError_t launch_probe_init_mean(Plan& p, const float* amp, float threshold, float2* w_out, cudaStream_t s);
 
 // Message returned by sharp_last_error() on this thread (sharp_api.cu).

@@ -1,6 +1,6 @@
 """GPU parity of the illumination refinement and initialisation (Sec. 2.2:
 drift and Fourier-space pathologies, reconstruction sequence steps 2 and 7;
-Sec. 4 threshold variant) against the FP64 oracle."""
+Sec. 3.2 threshold variant) against the FP64 oracle."""
 import numpy as np
 import pytest
 import torch

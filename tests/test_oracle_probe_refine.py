@@ -1,6 +1,6 @@
 """Pins of the oracle's illumination refinement and initialisation (Sec. 2.2:
 the drift and Fourier-space pathologies and reconstruction sequence steps 2
-and 7; Sec. 4 threshold variant) against closed forms, brute-force sums and
+and 7; Sec. 3.2 threshold variant) against closed forms, brute-force sums and
 invariants that do not go through the functions under test."""
 import math
 
