@@ -18,7 +18,6 @@ namespace sharp {
 namespace {
 
 constexpr int GATHER_THREADS = 256;       // 32 columns x 8 row groups
-constexpr int PROBE_CHUNK = 64;           // frames per partial sum of Eq. 10
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
     const float y = v - c;
@@ -199,15 +198,15 @@ __global__ void normalise_kernel(float2* __restrict__ C, float2* __restrict__ B,
 __global__ void probe_partial_kernel(const int32_t* __restrict__ pos, const float2* __restrict__ psi,
                                      const float2* __restrict__ zc, const float2* __restrict__ psiy,
                                      const float2* __restrict__ w, float* __restrict__ part, int K, int m,
-                                     int ny, int nx, int wrap) {
+                                     int ny, int nx, int wrap, int chunk_frames) {
     constexpr int U = 8;   // frames in flight per thread
     const int mm = m * m;
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= mm) return;
     const int chunk = blockIdx.y;
     const int y = l / m, x = l - y * m;
-    const int f0 = chunk * PROBE_CHUNK;
-    const int f1 = min(K, f0 + PROBE_CHUNK);
+    const int f0 = chunk * chunk_frames;
+    const int f1 = min(K, f0 + chunk_frames);
     const float2 wl = psiy ? __ldg(w + l) : make_float2(0.f, 0.f);
     float nr = 0.f, ni = 0.f, dn = 0.f;
     for (int f = f0; f < f1; f += U) {
@@ -581,7 +580,7 @@ static cudaError_t probe_common(Plan& p, const float2* psi, const float2* zc, co
     const int mm = p.m * p.m;
     dim3 g((mm + 255) / 256, p.probe_chunks);
     probe_partial_kernel<<<g, 256, 0, s>>>(p.pos, psi, zc, psiy, wform, p.probe_part, p.K, p.m, p.ny, p.nx,
-                                          p.prm.wrap);
+                                          p.prm.wrap, p.probe_chunk_frames);
     unsigned long long* dmax = reinterpret_cast<unsigned long long*>(p.scal);
     cudaError_t e = cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;

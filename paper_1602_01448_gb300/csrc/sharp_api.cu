@@ -283,7 +283,14 @@ int sharp_plan_create(sharp_plan* out, int K, int m, int ny, int nx, const int32
     std::memset(&p, 0, sizeof(p));
     p.K = K; p.m = m; p.ny = ny; p.nx = nx; p.prm = prm;
     p.tiles_y = tiles_y; p.tiles_x = tiles_x; p.tile_nnz = nnz;
-    p.probe_chunks = (K + 63) / 64;
+    {
+        // 64 frames per chunk of the Eq. 10 partial sums (fewer, longer chunks
+        // measured faster than 8-32 once the reduction is counted), more when
+        // the partial buffer would pass 64 MB
+        const long long max_chunks = std::max(1LL, (64LL << 20) / (12LL * m * m));
+        p.probe_chunk_frames = std::max(64, (int)((K + max_chunks - 1) / max_chunks));
+        p.probe_chunks = (K + p.probe_chunk_frames - 1) / p.probe_chunk_frames;
+    }
     const size_t n = (size_t)ny * nx, mm = (size_t)m * m;
     cudaError_t e = cudaSuccess;
 #define SHARP_ALLOC(field, count)                   \

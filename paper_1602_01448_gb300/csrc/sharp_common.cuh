@@ -101,7 +101,8 @@ struct Plan {
     int last_iter;           // last step run (0 = none)
     // reductions
     double* sums;            // 16 doubles of per-step sums
-    int probe_chunks;
+    int probe_chunks;        // chunks of frames in the partial sums of Eq. 10
+    int probe_chunk_frames;  // frames per chunk
     float* probe_part;       // FP32 partial sums of Eq. 10 per chunk of frames (chunks x 3 x m*m)
     double* probe_acc;       // 3 x m*m doubles (FP64 sums over the chunks)
     double* scal;            // 32 doubles of misc scalars
