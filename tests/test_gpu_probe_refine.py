@@ -32,6 +32,17 @@ def _drifted_probe(m, seed, d):
     return np.roll(w, d, axis=(0, 1))
 
 
+def _clear_of_rounding(w, margin=1e-2):
+    """The centring shift is an integer taken from the centroid (FP32 |w|^2 on
+    the GPU, FP64 in the oracle).  Both sides take the same decision when the
+    centroid offset is away from a rounding boundary; the test inputs are
+    chosen so, and this checks it."""
+    m = w.shape[0]
+    for c in O.probe_centroid(w):
+        t = c - m / 2 + 0.5
+        assert abs(t - round(t)) > margin, (c, m)
+
+
 def _band_mask(m, keep):
     """Low-pass Fourier mask in the unshifted layout: |q| <= keep per axis."""
     q = np.minimum(np.arange(m), m - np.arange(m))
@@ -43,6 +54,7 @@ def test_centring_matches_oracle(m):
     S = _lib()
     plan, _, _ = _plan(S, m)
     w = _drifted_probe(m, 1, (7, -4))
+    _clear_of_rounding(w)
     plan.set_probe_refinement(center=True)
     got = host(plan.probe_refine(dev(w)))
     ref, d = O.probe_center(w)
@@ -66,6 +78,7 @@ def test_fourier_constraints_match_oracle(m):
     assert rel_l2(host(wt), O.probe_fourier_amplitude(w, a_w)) < TOL
     # mask, then centring, in one call
     wd = _drifted_probe(m, 4, (-5, 9))
+    _clear_of_rounding(O.probe_fourier_mask(wd, mask))
     plan.set_probe_refinement(mask=dev(mask, torch.float32), center=True)
     got = host(plan.probe_refine(dev(wd)))
     assert rel_l2(got, O.refine_probe(wd, probe_mask=mask, probe_com=True)) < TOL
@@ -90,8 +103,16 @@ def test_mean_frame_initialisation_matches_oracle(m, threshold):
     assert rel_l2(got, ref) < TOL
 
 
-def test_raar_with_mask_and_centring_matches_oracle():
+def test_raar_with_mask_and_centring_matches_oracle(monkeypatch):
     S = _lib()
+    import oracle.sharp_oracle as OS
+    centre = OS.probe_center
+
+    def checked_centre(w):       # every centring in the oracle run is clear of rounding
+        _clear_of_rounding(w)
+        return centre(w)
+
+    monkeypatch.setattr(OS, "probe_center", checked_centre)
     m = 64
     rng = np.random.default_rng(7)
     side, step = 6, 10
