@@ -187,6 +187,10 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
     auto issue_c = [&](int f) {
         mbar_expect_tx(&bars[0], (unsigned)(MM * sizeof(float2)));
         bulk_g2s_hint(S, a.c + (size_t)f * MM, (unsigned)(MM * sizeof(float2)), &bars[0], pol_stream);
+        // the eps_Delta buffer the load phase will read (a frame ahead, so the
+        // chunked loads hit L2 instead of making four round trips to HBM)
+        if (FLAGS & RF_METRIC)
+            if (a.read_e) bulk_prefetch_l2(a.ebuf + (size_t)f * MM, (unsigned)(MM * sizeof(float2)));
     };
     // Frames are handed out by an atomic counter.  Blocks start staggered by
     // a fraction of a frame time so that the SMs' memory phases (gathers,
@@ -295,6 +299,8 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_batch_kerne
         const int f = g - __ldg(bt.base + s);
         mbar_expect_tx(&bars[0], (unsigned)(MM * sizeof(float2)));
         bulk_g2s_hint(S, t.c + (size_t)f * MM, (unsigned)(MM * sizeof(float2)), &bars[0], pol_stream);
+        if (FLAGS & RF_METRIC)
+            if (t.read_e) bulk_prefetch_l2(t.ebuf + (size_t)f * MM, (unsigned)(MM * sizeof(float2)));
     };
     if (tid == 0) {
         __nanosleep(2000u * (blockIdx.x & 3u));
