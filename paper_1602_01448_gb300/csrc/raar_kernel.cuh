@@ -61,13 +61,14 @@ __device__ __forceinline__ void raar_load_phase(const FrameArgs& a, int py, int 
     // (a store ahead of the next row's loads would serialise them).
 #pragma unroll
     for (int k0 = 0; k0 < 32; k0 += CH) {
-        float2 wf[CH], yv[CH], pv[CH], ev[CH];
+        float2 wf[CH], yv[CH], pv[CH], ev[CH], wp[CH];
 #pragma unroll
         for (int k = k0; k < k0 + CH; ++k) {
             const int y = q + TX * k;
             const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
             wf[k - k0] = ld_hint(a.w_form + y * M + x, pol_keep);
             yv[k - k0] = ld_hint(a.psiy + o, pol_keep);
+            if constexpr (FLAGS & RF_FORM_B) wp[k - k0] = ld_hint(a.w_proj + y * M + x, pol_keep);
             if constexpr (FLAGS & RF_METRIC) {
                 pv[k - k0] = ld_hint(a.psi + o, pol_keep);
                 ev[k - k0] = a.read_e ? ld_hint(a.ebuf + fo + y * M + x, pol_stream) : make_float2(0.f, 0.f);
@@ -90,7 +91,7 @@ __device__ __forceinline__ void raar_load_phase(const FrameArgs& a, int py, int 
             for (int k = k0; k < k0 + CH; ++k) {
                 const int y = q + TX * k;
                 const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
-                red_hint(a.accB + o, cmulc(ld_hint(a.w_proj + y * M + x, pol_keep), v[k]), pol_keep);
+                red_hint(a.accB + o, cmulc(wp[k - k0], v[k]), pol_keep);
             }
         }
         if (a.write_e) {
