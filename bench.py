@@ -5,7 +5,7 @@ an end-to-end figure through the C ABI with host buffers, and the FP64 oracle
 timed on the host cores as a reported CPU baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload fermat|raster256|batch]
+                  [--workload fermat|raster256|batch|batch-small]
 
 --workload raster256 times the large scan instead: a 100 x 100 raster of
 256^2 frames (step 24 +-1 px) over a 3072^2 object, Poisson 10^8 photons,
@@ -386,11 +386,15 @@ def run_ours(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
-def batch_scans(n_scans: int = 32, seed: int = 7):
+def batch_scans(n_scans: int = 32, seed: int = 7, small: bool = False):
     """32 independent scans: frame size drawn from {64, 128, 256}, frame count
     uniform in [100, 4000]; each a raster of side ceil(sqrt(K)) with step
-    round(0.1875 m), object = scan extent + 64 px, Poisson 10^U[5,7]."""
+    round(0.1875 m), object = scan extent + 64 px, Poisson 10^U[5,7].
+    small=True: 128 scans of 100 frames of 64^2 (many small scans, where the
+    per-scan launches dominate)."""
     import synth
+    if small:
+        return [synth.scan_batch_member(300 + i, 64, 100) for i in range(128)]
     rng = np.random.default_rng(seed)
     ms = rng.choice([64, 128, 256], size=n_scans)
     ks = rng.integers(100, 4001, size=n_scans)
@@ -407,7 +411,7 @@ def run_batch(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    scans = batch_scans()
+    scans = batch_scans(small=args.workload == "batch-small")
     total = sum(sc.K for sc in scans)
     alg_bytes = sum(20.0 * sc.m * sc.m * sc.K for sc in scans)
 
@@ -507,7 +511,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="fermat", choices=["fermat", "raster256", "batch"])
+    ap.add_argument("--workload", default="fermat", choices=["fermat", "raster256", "batch", "batch-small"])
     ap.add_argument("--frames", type=int, default=None,
                     help="frames of the scan (default: the workload's; fewer for small ncu captures; "
                          "raster256 rounds to a square raster)")
@@ -521,7 +525,7 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl")
-    if args.workload == "batch":
+    if args.workload in ("batch", "batch-small"):
         run_batch(args, rank, world)
     else:
         run_ours(args, rank, world)
