@@ -48,6 +48,21 @@ extern "C" {
 #define SHARP_ERR_STATE            5  /* call order violated (e.g. step before init) */
 
 #define SHARP_PREC_FP32            0  /* FP32 data and transforms, FP64 global sums */
+/*
+ * Tensor-core precision modes (m = 128 only).  The 2D DFTs of the RAAR frame
+ * pass (sharp_raar_step) and of the data projection (sharp_fourier_project)
+ * run as contractions with the m x m DFT matrix of Eq. 2 on the tensor cores,
+ * FP32 accumulation; data, metrics and every other operator stay FP32 / FP64.
+ *   SHARP_PREC_FP16S  : FP16 operands; each operand matrix is scaled per frame
+ *                       by a power of two (its largest component mapped into
+ *                       [2^14, 2^15)) so that FP16's range is never left.
+ *                       Relative error of one transform ~1e-3 (RMS ~3e-4).
+ *   SHARP_PREC_BF16X3 : BF16 operands split x = hi + lo, three products
+ *                       hi.hi + hi.lo + lo.hi per real product.  Relative
+ *                       error of one transform ~1e-5.
+ */
+#define SHARP_PREC_FP16S           1
+#define SHARP_PREC_BF16X3          2
 
 typedef struct sharp_plan_s* sharp_plan;
 
@@ -57,7 +72,7 @@ typedef struct {
     int   wrap;          /* 1: object indexed modulo its size (periodic boundary, Fig. 3) */
     int   probe_every;   /* refine the probe (Eq. 10) on steps with iter % probe_every == 0; 0 = never */
     int   residual_every;/* eps_Q and eps_Delta (Eqs. 12, 13) on steps with iter % residual_every == 0; 0 = never */
-    int   precision;     /* SHARP_PREC_FP32 */
+    int   precision;     /* SHARP_PREC_FP32, or SHARP_PREC_FP16S / SHARP_PREC_BF16X3 (m = 128) */
 } sharp_params;
 
 /* Message of the last failed call on this thread ("" if none).  Never NULL. */
@@ -81,7 +96,10 @@ void sharp_default_params(sharp_params* p);
  * per-tile frame lists, reduction buffers; for m = 256 also one m x m
  * transposition slab per SM, 78 MB on 152 SMs).  The per-block lists of frames
  * that touch each image block (Sec. 2.3) are built here once, on the host.
- * Errors: INVALID_ARG (K < 1, ny or nx < m, bad position), UNSUPPORTED_SIZE.
+ * With a tensor-core precision mode the plan also holds the DFT matrix parts
+ * (64 KB for FP16S, 128 KB for BF16X3).
+ * Errors: INVALID_ARG (K < 1, ny or nx < m, bad position, unknown precision),
+ * UNSUPPORTED_SIZE (m without a kernel, or a tensor-core mode with m != 128).
  */
 int sharp_plan_create(sharp_plan* plan, int K, int m, int ny, int nx,
                       const int32_t* pos, const sharp_params* params,
@@ -242,7 +260,7 @@ int sharp_amp_loss_backward(sharp_plan plan, const float2* obj, const float2* pr
  * grid or on graphs.
  *   plans : nscans plans, already set up with sharp_raar_init; they must share
  *           probe_every and residual_every and be stepped only through the
- *           batch.  The batch does not own them.
+ *           batch, and use SHARP_PREC_FP32.  The batch does not own them.
  * sharp_batch_bind gives scan `scan` its state buffers (as sharp_raar_step;
  * probe and metrics may be NULL); rebinding drops the recorded graphs.
  * sharp_batch_tuned_grid returns the grid chosen for frame size m (or -1).

@@ -22,6 +22,7 @@ __all__ = [
     "sharp_amp_loss_backward", "AmpLoss", "amp_loss", "sharp_plan_set_profiling",
     "sharp_plan_kernel_times", "sharp_plan_status", "sharp_fourier_project_noalloc", "Batch",
     "SHARP_PROBE_CONSTRAINT_NONE", "SHARP_PROBE_CONSTRAINT_MASK", "SHARP_PROBE_CONSTRAINT_AMPLITUDE",
+    "SHARP_PREC_FP32", "SHARP_PREC_FP16S", "SHARP_PREC_BF16X3", "PRECISIONS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -92,6 +93,14 @@ _lib_fns = {
 }
 _C = {name: _decl(name, *sig) for name, sig in _lib_fns.items()}
 
+
+# sharp_params.precision: FP32 transforms, or the frame DFTs as tensor-core
+# contractions (m = 128): FP16 with per-frame power-of-two scaling, or BF16
+# three-term split; FP32 accumulation in both.
+SHARP_PREC_FP32 = 0
+SHARP_PREC_FP16S = 1
+SHARP_PREC_BF16X3 = 2
+PRECISIONS = {"fp32": SHARP_PREC_FP32, "fp16s": SHARP_PREC_FP16S, "bf16x3": SHARP_PREC_BF16X3}
 
 SHARP_PROBE_CONSTRAINT_NONE = 0
 SHARP_PROBE_CONSTRAINT_MASK = 1
@@ -238,7 +247,7 @@ class Plan:
     """Owns a ``sharp_plan`` and the RAAR state tensors of one scan."""
 
     def __init__(self, pos, m, shape, beta=0.75, wrap=False, probe_every=0, residual_every=1,
-                 device="cuda"):
+                 device="cuda", precision="fp32"):
         pos = torch.as_tensor(pos, dtype=torch.int32).to(device).contiguous()
         self.K = int(pos.shape[0])
         self.m = int(m)
@@ -249,6 +258,7 @@ class Plan:
         prm.wrap = int(bool(wrap))
         prm.probe_every = int(probe_every)
         prm.residual_every = int(residual_every)
+        prm.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.params = prm
         self.pos = pos
         self.handle = sharp_plan_create(self.K, self.m, self.shape[0], self.shape[1], pos, prm)

@@ -1,0 +1,526 @@
+// RAAR frame pass with the frame transforms as DFT-matrix contractions on the
+// fifth-generation tensor cores (tcgen05, TMEM accumulators), 128 x 128
+// frames, in two mixed-precision modes:
+//   SHARP_PREC_FP16S  : FP16 operands, each operand matrix scaled per frame by
+//                       a power of two (its largest component maps into
+//                       [2^14, 2^15)), one product per real matrix product;
+//   SHARP_PREC_BF16X3 : BF16 operands split x = hi + lo, three products
+//                       hi.hi + hi.lo + lo.hi per real matrix product;
+// both accumulated in FP32 in tensor memory.
+//
+// The step computes the same quantities as the FP32 frame pass (Sec. 2.2 RAAR
+// update; Eqs. 2, 5, 7-9; metrics of Eqs. 11-13):
+//   z   = w_f . psi_y(r + x_i) + c_i
+//   Z   = F z F^T                 (F the unitary m x m DFT matrix of Eq. 2, F^T = F)
+//   U   = (1-2b) a Z/|Z| + b Z    (phase 1 where Z = 0)
+//   c_i <- F* U F*^T
+//   C(r + x_i) += conj(w) c_i
+// and, as the standalone data projection P_a of Eq. 7, out = F* (a Z/|Z|) F*^T.
+//
+// One frame per block at a time (persistent, one block per SM).  A 2D
+// transform is two contractions with the roles of the frame's indices
+// swapped, so every intermediate leaves tensor memory already in the layout
+// the next contraction reads:
+//   stage 1: D1[k1][n2] = sum_n1 F[k1][n1]  z[n1][n2]      (B rows = n2)
+//   stage 2: D2[k2][k1] = sum_n2 F[k2][n2]  D1[k1][n2]     = Z[k1][k2]
+//   stage 3: D3[n1][k2] = sum_k1 F*[n1][k1] U[k1][k2]      (B rows = k2)
+//   stage 4: D4[n2][n1] = sum_k2 F*[n2][k2] D3[n1][k2]     = c_new[n1][n2]
+// A (the DFT matrix) is M x K with K-major rows and sits in shared memory for
+// the whole launch; B of each stage is written by the threads from tensor
+// memory (TMEM lane = B row, TMEM column = K) into shared memory in the
+// canonical no-swizzle K-major layout, converted to FP16 / BF16 on the way.
+// A complex product is four real ones, D_r = A_r B_r -+ A_i B_i and
+// D_i = A_r B_i +- A_i B_r (the sign of the A_i terms through the
+// instruction's negate-A bit: forward F, inverse F*).
+//
+// Thread t of the 512 (16 warps) owns TMEM lane r = 32 (w % 4) + lane and the
+// columns 64 j + 16 (w / 4) + [0, 16) for j = 0, 1; in frame coordinates that
+// is one column index n2 = r (coalesced global accesses across a warp) and 32
+// row indices.  TMEM holds two 256-column regions P and Q (real part in
+// columns 0-127 of a region, imaginary part in 128-255); stages alternate
+// between them (z in P -> D1 in Q -> D2 in P -> D3 in Q -> D4 in P).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "sharp_common.cuh"
+#include "tcgen05.cuh"
+
+namespace sharp {
+
+template <int PREC>
+struct MixGeo {
+    static constexpr int M = 128;
+    static constexpr int NT = 512;
+    static constexpr bool F16 = PREC == SHARP_PREC_FP16S;
+    static constexpr int NPART = F16 ? 2 : 4;           // operand parts: {re, im} or {re_hi, re_lo, im_hi, im_lo}
+    static constexpr int NBUF = F16 ? 2 : 1;            // K-chunk buffers of B (two K-chunks of 64 per stage)
+    static constexpr int A_PART = M * M * 2;            // 32 KB: one 128 x 128 16-bit matrix
+    static constexpr int B_PART = M * 64 * 2;           // 16 KB: 128 rows x one K-chunk of 64
+    static constexpr int A_BYTES = NPART * A_PART;
+    static constexpr int B_SLOT = NPART * B_PART;
+    static constexpr int B_BYTES = NBUF * B_SLOT;
+    // Unused tail: keeps any operand read of a descriptor within the block's
+    // shared memory.
+    static constexpr int GUARD = 32768;
+    static constexpr int SMEM = A_BYTES + B_BYTES + GUARD + 128;
+    static constexpr uint32_t LBO = 16 * 128;           // K-adjacent core matrices (16 row groups of 128 B)
+    static constexpr uint32_t SBO = 128;                // row-group-adjacent core matrices
+    static constexpr uint32_t T_P = 0, T_Q = 256;       // TMEM regions
+    static_assert(SMEM <= 232448, "shared memory of one block");
+    static_assert(SMEM > 232448 / 2, "one block per SM: the kernel allocates all 512 TMEM columns");
+};
+
+// Largest |component| of the block (all threads receive it).
+__device__ __forceinline__ float mix_block_max(float v, float* s_max) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float m = s_max[0];
+#pragma unroll
+    for (int k = 1; k < 16; ++k) m = fmaxf(m, s_max[k]);
+    return m;
+}
+
+// Power of two 2^e with mx 2^e in [2^14, 2^15) (1 for 0, Inf or NaN).
+__device__ __forceinline__ float mix_pow2_scale(float mx) {
+    if (!(mx > 0.f) || !(mx < 3.0e38f)) return 1.f;
+    const int ex = ((__float_as_int(mx) >> 23) & 0xff) - 127;
+    int e = 14 - ex;
+    e = e < -100 ? -100 : (e > 100 ? 100 : e);
+    return __int_as_float((e + 127) << 23);
+}
+
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_h2(float x, float y) {
+    const __half2 h = __floats2half2_rn(x, y);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t pack_b2(__nv_bfloat16 x, __nv_bfloat16 y) {
+    __nv_bfloat162 h;
+    h.x = x;
+    h.y = y;
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Write this thread's 16 K-values (row r, K-local 16 h .. 16 h + 15 of a
+// K-chunk) of the real and imaginary planes, times g, into the B buffer `sb`.
+template <int PREC>
+__device__ __forceinline__ void mix_put(uint32_t sb, int r, int h, const float (&re)[16], const float (&im)[16],
+                                        float g) {
+    using G = MixGeo<PREC>;
+    const uint32_t off0 = (uint32_t)(((2 * h) * 16 + (r >> 3)) * 128 + (r & 7) * 16);   // core matrix (r/8, 2h)
+    const uint32_t off1 = off0 + G::LBO;                                                 // (r/8, 2h + 1)
+    if constexpr (G::F16) {
+        uint32_t pr[8], pi[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            pr[t] = pack_h2(re[2 * t] * g, re[2 * t + 1] * g);
+            pi[t] = pack_h2(im[2 * t] * g, im[2 * t + 1] * g);
+        }
+        sts128(sb + off0, pr[0], pr[1], pr[2], pr[3]);
+        sts128(sb + off1, pr[4], pr[5], pr[6], pr[7]);
+        sts128(sb + G::B_PART + off0, pi[0], pi[1], pi[2], pi[3]);
+        sts128(sb + G::B_PART + off1, pi[4], pi[5], pi[6], pi[7]);
+    } else {
+        uint32_t rh[8], rl[8], ih[8], il[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            __nv_bfloat16 h0 = __float2bfloat16_rn(re[2 * t]), h1 = __float2bfloat16_rn(re[2 * t + 1]);
+            rh[t] = pack_b2(h0, h1);
+            rl[t] = pack_b2(__float2bfloat16_rn(re[2 * t] - __bfloat162float(h0)),
+                            __float2bfloat16_rn(re[2 * t + 1] - __bfloat162float(h1)));
+            h0 = __float2bfloat16_rn(im[2 * t]);
+            h1 = __float2bfloat16_rn(im[2 * t + 1]);
+            ih[t] = pack_b2(h0, h1);
+            il[t] = pack_b2(__float2bfloat16_rn(im[2 * t] - __bfloat162float(h0)),
+                            __float2bfloat16_rn(im[2 * t + 1] - __bfloat162float(h1)));
+        }
+        sts128(sb + off0, rh[0], rh[1], rh[2], rh[3]);
+        sts128(sb + off1, rh[4], rh[5], rh[6], rh[7]);
+        sts128(sb + G::B_PART + off0, rl[0], rl[1], rl[2], rl[3]);
+        sts128(sb + G::B_PART + off1, rl[4], rl[5], rl[6], rl[7]);
+        sts128(sb + 2 * G::B_PART + off0, ih[0], ih[1], ih[2], ih[3]);
+        sts128(sb + 2 * G::B_PART + off1, ih[4], ih[5], ih[6], ih[7]);
+        sts128(sb + 3 * G::B_PART + off0, il[0], il[1], il[2], il[3]);
+        sts128(sb + 3 * G::B_PART + off1, il[4], il[5], il[6], il[7]);
+    }
+}
+
+// MMAs of K-chunk j of one stage (thread 0): D (columns d, d + 128) +=
+// F(or F*)[:, 64 j .. 64 j + 63] . B(chunk)^T.
+template <int PREC>
+__device__ __forceinline__ void mix_issue(uint32_t sA, uint32_t sb, uint32_t d, int j, bool inverse) {
+    using G = MixGeo<PREC>;
+    constexpr int BF = G::F16 ? 0 : 1;
+    constexpr uint32_t ID_POS = idesc_f16(BF, 0, 128, 128);
+    constexpr uint32_t ID_NEG = idesc_f16(BF, 1, 128, 128);
+    const uint32_t id_ai_r = inverse ? ID_POS : ID_NEG;   // sign of A_i B_i in D_r
+    const uint32_t id_ai_i = inverse ? ID_NEG : ID_POS;   // sign of A_i B_r in D_i
+    const uint32_t dr = d, di = d + 128;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int kk = 4 * j + s;
+        const uint32_t acc0 = (j > 0 || s > 0) ? 1u : 0u;
+        auto ad = [&](int part) { return smem_desc(sA + part * G::A_PART + kk * 2 * G::LBO, G::LBO, G::SBO); };
+        auto bd = [&](int part) { return smem_desc(sb + part * G::B_PART + s * 2 * G::LBO, G::LBO, G::SBO); };
+        if constexpr (G::F16) {   // A: 0 F_r, 1 F_i;  B: 0 re, 1 im
+            mma_f16_ss(dr, ad(0), bd(0), ID_POS, acc0);
+            mma_f16_ss(dr, ad(1), bd(1), id_ai_r, 1u);
+            mma_f16_ss(di, ad(0), bd(1), ID_POS, acc0);
+            mma_f16_ss(di, ad(1), bd(0), id_ai_i, 1u);
+        } else {                  // A: 0 F_r hi, 1 F_r lo, 2 F_i hi, 3 F_i lo;  B: 0 re hi, 1 re lo, 2 im hi, 3 im lo
+            auto prod = [&](uint32_t dd, int a0, int b0, uint32_t id, uint32_t acc) {
+                mma_f16_ss(dd, ad(a0), bd(b0), id, acc);
+                mma_f16_ss(dd, ad(a0), bd(b0 + 1), id, 1u);
+                mma_f16_ss(dd, ad(a0 + 1), bd(b0), id, 1u);
+            };
+            prod(dr, 0, 0, ID_POS, acc0);
+            prod(dr, 2, 2, id_ai_r, 1u);
+            prod(di, 0, 2, ID_POS, acc0);
+            prod(di, 2, 0, id_ai_i, 1u);
+        }
+    }
+}
+
+// Shared state of one block.
+struct MixCtx {
+    uint32_t sA, sB;       // shared addresses of the DFT matrix parts and the B buffers
+    uint32_t tbase;        // TMEM base (lane 0, column 0)
+    uint32_t tl;           // TMEM address of this warp's lane quarter
+    int r, h;              // TMEM lane (frame index owned) and column group
+    uint64_t* bar;         // MMA completion
+    float* s_max;
+    unsigned phase;
+};
+
+// Columns of this thread in K-chunk j.
+__device__ __forceinline__ int mix_col(int j, int h) { return 64 * j + 16 * h; }
+
+// Largest component of region `src` over the block.
+__device__ __forceinline__ float mix_region_max(const MixCtx& x, uint32_t src) {
+    float mx = 0.f;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        float re[16], im[16];
+        const uint32_t c = (uint32_t)mix_col(j, x.h);
+        tmem_ld16x2(x.tl + src + c, x.tl + src + 128 + c, re, im);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) mx = fmaxf(mx, fmaxf(fabsf(re[t]), fabsf(im[t])));
+    }
+    return mix_block_max(mx, x.s_max);
+}
+
+// One contraction stage: region dst = F(or F*) . (g * region src)^T in the
+// stage layout above.  False if an MMA completion wait gave up.
+template <int PREC>
+__device__ __forceinline__ bool mix_stage(MixCtx& x, uint32_t src, uint32_t dst, bool inverse, float g) {
+    using G = MixGeo<PREC>;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const uint32_t sb = x.sB + (uint32_t)((G::NBUF == 2 ? j : 0) * G::B_SLOT);
+        float re[16], im[16];
+        const uint32_t c = (uint32_t)mix_col(j, x.h);
+        tmem_ld16x2(x.tl + src + c, x.tl + src + 128 + c, re, im);
+        mix_put<PREC>(sb, x.r, x.h, re, im, g);
+        fence_proxy_async_smem();   // generic-proxy writes -> tensor-core (async proxy) reads
+        tc_fence_before();
+        __syncthreads();
+        const bool commit = (G::NBUF == 1) || (j == 1);
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            mix_issue<PREC>(x.sA, sb, x.tbase + dst, j, inverse);
+            if (commit) mma_commit(x.bar);
+        }
+        if (commit) {
+            const bool ok = __syncthreads_and(mbar_wait(x.bar, x.phase));
+            if (!ok) return false;
+            x.phase ^= 1u;
+            tc_fence_after();
+        }
+    }
+    return true;
+}
+
+template <int PREC, int MODE, int FLAGS, int WRAP>
+__global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) {
+    using G = MixGeo<PREC>;
+    constexpr int M = 128;
+    constexpr int MM = M * M;
+    constexpr bool RAAR = MODE == MODE_RAAR;
+    extern __shared__ __align__(128) unsigned char mix_smem[];
+    __shared__ FrameArgs a;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ float s_max[16];
+    __shared__ float red[32 * 5];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    MixCtx x;
+    x.sA = (smem_addr(mix_smem) + 127u) & ~127u;
+    x.sB = x.sA + G::A_BYTES;
+    x.r = 32 * (warp & 3) + lane;
+    x.h = warp >> 2;
+    x.bar = &bar;
+    x.s_max = s_max;
+    x.phase = 0;
+
+    {   // DFT matrix parts, already in the operand layout, into shared memory
+        const uint4* src = reinterpret_cast<const uint4*>(ap.dft_tab);
+        unsigned char* dst = mix_smem + (x.sA - smem_addr(mix_smem));
+        for (int k = tid; k < G::A_BYTES / 16; k += G::NT)
+            reinterpret_cast<uint4*>(dst)[k] = __ldg(src + k);
+    }
+    if (tid == 0) {
+        a = ap;
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&s_tmem, 512);
+        tmem_relinquish();
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    x.tbase = s_tmem;
+    x.tl = x.tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
+    const float b = RAAR ? a.beta : 0.f;
+    const float cp = 1.f - 2.f * b;
+    const int xcol = x.r;   // frame column n2 owned by this thread
+    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    bool ok = true;
+
+    for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
+        const size_t fo = (size_t)i * MM;
+        if (tid == 0) bulk_prefetch_l2(a.amp + fo, (unsigned)(MM * sizeof(float)));
+        const int py = RAAR ? a.pos[2 * i] : 0;
+        const int px = RAAR ? a.pos[2 * i + 1] : 0;
+
+        // ------------------------------------------------ load: z into P
+        float mx = 0.f;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int y0 = mix_col(j, x.h) + 8 * hh;
+                float zr[8], zi[8];
+                if constexpr (RAAR) {
+                    float2 cv[8], wf[8], yv[8], wp[8], pv[8], ev[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int y = y0 + k;
+                        const int o = obj_index(py, px, y, xcol, a.ny, a.nx, WRAP);
+                        cv[k] = ld_hint(a.c + fo + y * M + xcol, pol_stream);
+                        wf[k] = ld_hint(a.w_form + y * M + xcol, pol_keep);
+                        yv[k] = ld_hint(a.psiy + o, pol_keep);
+                        if constexpr (FLAGS & RF_FORM_B) wp[k] = ld_hint(a.w_proj + y * M + xcol, pol_keep);
+                        if constexpr (FLAGS & RF_METRIC) {
+                            pv[k] = ld_hint(a.psi + o, pol_keep);
+                            ev[k] = a.read_e ? ld_hint(a.ebuf + fo + y * M + xcol, pol_stream)
+                                             : make_float2(0.f, 0.f);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int y = y0 + k;
+                        const float2 wy = cmul(wf[k], yv[k]);
+                        const float2 z = cadd(wy, cv[k]);
+                        zr[k] = z.x;
+                        zi[k] = z.y;
+                        acc[2] += cabs2(z);
+                        if constexpr (FLAGS & RF_METRIC) {
+                            acc[3] += cabs2(csub(cmul(wf[k], pv[k]), z));
+                            acc[4] += cabs2(cadd(wy, ev[k]));
+                        }
+                        if constexpr (FLAGS & RF_FORM_B) {
+                            const int o = obj_index(py, px, y, xcol, a.ny, a.nx, WRAP);
+                            red_hint(a.accB + o, cmulc(wp[k], z), pol_keep);
+                        }
+                        if (a.write_e) st_hint(a.ebuf + fo + y * M + xcol, make_float2(-z.x, -z.y), pol_stream);
+                    }
+                } else {
+                    float2 zv[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) zv[k] = ld_hint(a.zin + fo + (y0 + k) * M + xcol, pol_stream);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        zr[k] = zv[k].x;
+                        zi[k] = zv[k].y;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) mx = fmaxf(mx, fmaxf(fabsf(zr[k]), fabsf(zi[k])));
+                tmem_st8x2(x.tl + G::T_P + y0, x.tl + G::T_P + 128 + y0, zr, zi);
+            }
+        }
+        tmem_wait_st();
+        float g0 = 1.f, g1 = 1.f, g2 = 1.f, g3 = 1.f;
+        if constexpr (G::F16) g0 = mix_pow2_scale(mix_block_max(mx, s_max));
+
+        // ------------------------------------------------ forward transform
+        ok = mix_stage<PREC>(x, G::T_P, G::T_Q, false, g0);
+        if (!ok) break;
+        if constexpr (G::F16) g1 = mix_pow2_scale(mix_region_max(x, G::T_Q));
+        ok = mix_stage<PREC>(x, G::T_Q, G::T_P, false, g1);
+        if (!ok) break;
+
+        // ------------------------------------------------ Fourier step on P
+        {
+            const float inv = 1.f / (g0 * g1);   // exact: powers of two
+            float um = 0.f;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int k0 = mix_col(j, x.h);
+                float re[16], im[16];
+                tmem_ld16x2(x.tl + G::T_P + k0, x.tl + G::T_P + 128 + k0, re, im);
+                float av[16];
+#pragma unroll
+                for (int t = 0; t < 16; ++t) av[t] = __ldcs(a.amp + fo + (size_t)(k0 + t) * M + xcol);
+                float ur[16], ui[16];
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const float X = re[t] * inv, Y = im[t] * inv;
+                    const float m2 = fmaf(X, X, Y * Y);
+                    const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
+                    const float d = av[t] - m2 * rs;
+                    acc[0] += d * d;
+                    acc[1] += av[t] * av[t];
+                    if (m2 > 0.f) {
+                        const float f = fmaf(cp * av[t], rs, b);
+                        ur[t] = X * f;
+                        ui[t] = Y * f;
+                    } else {
+                        ur[t] = cp * av[t];
+                        ui[t] = 0.f;
+                    }
+                    um = fmaxf(um, fmaxf(fabsf(ur[t]), fabsf(ui[t])));
+                }
+                float r8[8], i8[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) { r8[t] = ur[t]; i8[t] = ui[t]; }
+                tmem_st8x2(x.tl + G::T_P + k0, x.tl + G::T_P + 128 + k0, r8, i8);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) { r8[t] = ur[8 + t]; i8[t] = ui[8 + t]; }
+                tmem_st8x2(x.tl + G::T_P + k0 + 8, x.tl + G::T_P + 128 + k0 + 8, r8, i8);
+            }
+            tmem_wait_st();
+            if constexpr (G::F16) g2 = mix_pow2_scale(mix_block_max(um, s_max));
+        }
+
+        // ------------------------------------------------ inverse transform
+        ok = mix_stage<PREC>(x, G::T_P, G::T_Q, true, g2);
+        if (!ok) break;
+        if constexpr (G::F16) g3 = mix_pow2_scale(mix_region_max(x, G::T_Q));
+        ok = mix_stage<PREC>(x, G::T_Q, G::T_P, true, g3);
+        if (!ok) break;
+
+        // ------------------------------------------------ epilogue from P
+        {
+            const float inv = 1.f / (g2 * g3);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int y0 = mix_col(j, x.h);
+                float re[16], im[16];
+                tmem_ld16x2(x.tl + G::T_P + y0, x.tl + G::T_P + 128 + y0, re, im);
+                if constexpr (RAAR) {
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        float2 wp[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) wp[k] = ld_hint(a.w_proj + (y0 + 8 * hh + k) * M + xcol, pol_keep);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int t = 8 * hh + k;
+                            const int y = y0 + t;
+                            const int o = obj_index(py, px, y, xcol, a.ny, a.nx, WRAP);
+                            const float2 cn = make_float2(re[t] * inv, im[t] * inv);
+                            st_hint(a.c + fo + y * M + xcol, cn, pol_stream);
+                            red_hint(a.accA + o, cmulc(wp[k], cn), pol_keep);
+                            if (a.write_e) red_hint(a.ebuf + fo + y * M + xcol, cn, pol_stream);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 16; ++t)
+                        st_hint(a.zout + fo + (y0 + t) * M + xcol, make_float2(re[t] * inv, im[t] * inv),
+                                pol_stream);
+                }
+            }
+        }
+        // every thread is past its reads of P before the next frame's load
+        // phase overwrites it (each thread only touches its own lane and
+        // columns, so program order suffices)
+    }
+
+    if (!ok) {
+        // a completion wait gave up: wait (bounded) once more for the MMAs
+        // in flight, flag the failure, release TMEM and leave the sums alone
+        mbar_wait(&bar, x.phase);
+        if (tid == 0) atomicExch(a.err, SHARP_ERR_TIMEOUT);
+    } else {
+        block_sum<G::NT, 5>(acc, red);
+        if (tid == 0) {
+            if constexpr (RAAR) {
+#pragma unroll
+                for (int j = 0; j < 5; ++j) atomicAdd(a.sums + j, (double)acc[j]);
+            } else {
+                atomicAdd(a.sums, (double)acc[0]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(x.tbase, 512);
+    }
+}
+
+template <int PREC, int MODE, int FLAGS, int WRAP>
+static cudaError_t launch_mixed_one(const FrameArgs& a, cudaStream_t s) {
+    using G = MixGeo<PREC>;
+    auto kern = raar_mixed_kernel<PREC, MODE, FLAGS, WRAP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int grid = a.K < sms ? a.K : sms;
+    kern<<<grid, G::NT, G::SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_mixed_prec(int mode, int flags, const FrameArgs& a, cudaStream_t s) {
+    if (mode == MODE_PROJECT) return launch_mixed_one<PREC, MODE_PROJECT, 0, 0>(a, s);
+    if (mode != MODE_RAAR) return cudaErrorInvalidValue;
+    const int f = flags & (RF_FORM_B | RF_METRIC);
+    if (a.wrap) {
+        switch (f) {
+            case 0: return launch_mixed_one<PREC, MODE_RAAR, 0, 1>(a, s);
+            case RF_FORM_B: return launch_mixed_one<PREC, MODE_RAAR, RF_FORM_B, 1>(a, s);
+            case RF_METRIC: return launch_mixed_one<PREC, MODE_RAAR, RF_METRIC, 1>(a, s);
+            default: return launch_mixed_one<PREC, MODE_RAAR, RF_FORM_B | RF_METRIC, 1>(a, s);
+        }
+    }
+    switch (f) {
+        case 0: return launch_mixed_one<PREC, MODE_RAAR, 0, 0>(a, s);
+        case RF_FORM_B: return launch_mixed_one<PREC, MODE_RAAR, RF_FORM_B, 0>(a, s);
+        case RF_METRIC: return launch_mixed_one<PREC, MODE_RAAR, RF_METRIC, 0>(a, s);
+        default: return launch_mixed_one<PREC, MODE_RAAR, RF_FORM_B | RF_METRIC, 0>(a, s);
+    }
+}
+
+}  // namespace sharp

@@ -1,8 +1,11 @@
 // C ABI of the library (include/sharp.h): argument checks, plan scratch,
 // per-block frame lists, and the order of kernel launches of each call.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -80,7 +83,8 @@ void free_plan(Plan& p) {
     void* ptrs[] = {p.pos,   p.tile_ptr,   p.tile_frames, p.w_cur, p.w_form,     p.w2,
                     p.Dsum,  p.invD,       p.dmax_bits,   p.accA,  p.accB,       p.ebuf,
                     p.sums,  p.probe_part, p.probe_acc,   p.scal,  p.w2tmp,      p.Dtmp,
-                    p.invDtmp, p.errflag, p.counter, p.big_scratch, p.probe_cons, p.w_tmp};
+                    p.invDtmp, p.errflag, p.counter, p.big_scratch, p.probe_cons, p.w_tmp,
+                    p.dft_tab};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     std::memset(&p, 0, sizeof(p));
@@ -100,8 +104,42 @@ sharp::FrameArgs base_args(const Plan& p) {
     a.err = p.errflag;
     a.scratch = p.big_scratch;
     a.counter = p.counter;
+    a.dft_tab = p.dft_tab;
     return a;
 }
+
+// The m x m unitary DFT matrix F[k][n] = e^{-2 pi i kn/m} / sqrt(m) (Eq. 2) as
+// the A operand of the tensor-core contraction kernels: parts {F_r, F_i} in
+// FP16 (SHARP_PREC_FP16S) or {F_r hi, F_r lo, F_i hi, F_i lo} in BF16
+// (SHARP_PREC_BF16X3, lo = bf16(F - hi)), each part in the canonical K-major
+// no-swizzle layout: core matrix (k/8, n/8) of 8 rows x 8 values at byte
+// ((n/8) * (m/8) + k/8) * 128, row k%8 at +16 (k%8), value n%8 at +2 (n%8).
+std::vector<uint16_t> dft_table(int prec, int m) {
+    const int parts = prec == SHARP_PREC_FP16S ? 2 : 4;
+    const size_t mm = (size_t)m * m;
+    std::vector<uint16_t> t(parts * mm, 0);
+    const double pi = 3.14159265358979323846, s = 1.0 / std::sqrt((double)m);
+    for (int k = 0; k < m; ++k)
+        for (int n = 0; n < m; ++n) {
+            const double ang = 2.0 * pi * (double)(((long long)k * n) % m) / m;
+            const double v[2] = {std::cos(ang) * s, -std::sin(ang) * s};
+            const size_t off = ((size_t)(n / 8) * (m / 8) + k / 8) * 64 + (k % 8) * 8 + (n % 8);
+            for (int c = 0; c < 2; ++c) {
+                if (prec == SHARP_PREC_FP16S) {
+                    const __half_raw h = __double2half(v[c]);
+                    t[c * mm + off] = h.x;
+                } else {
+                    const __nv_bfloat16 hi = __double2bfloat16(v[c]);
+                    const __nv_bfloat16 lo = __double2bfloat16(v[c] - (double)__bfloat162float(hi));
+                    t[(2 * c) * mm + off] = static_cast<__nv_bfloat16_raw>(hi).x;
+                    t[(2 * c + 1) * mm + off] = static_cast<__nv_bfloat16_raw>(lo).x;
+                }
+            }
+        }
+    return t;
+}
+
+bool mixed(const Plan& p) { return p.prm.precision != SHARP_PREC_FP32; }
 
 int check_plan(sharp_plan plan) {
     if (!plan) return fail(SHARP_ERR_INVALID_ARG, "plan is NULL");
@@ -111,6 +149,14 @@ int check_plan(sharp_plan plan) {
 }  // namespace
 
 void sharp::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+cudaError_t sharp::launch_mixed(int prec, int mode, int flags, const FrameArgs& a, cudaStream_t s) {
+    if (a.K <= 0) return cudaSuccess;
+    if (a.m != 128 || !a.dft_tab) return cudaErrorInvalidValue;
+    if (prec == SHARP_PREC_FP16S) return launch_mixed_prec<SHARP_PREC_FP16S>(mode, flags, a, s);
+    if (prec == SHARP_PREC_BF16X3) return launch_mixed_prec<SHARP_PREC_BF16X3>(mode, flags, a, s);
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t sharp::raar_step_clear(Plan& p, cudaStream_t s) {
     return cudaMemsetAsync(p.sums, 0, 8 * sizeof(double), s);
@@ -239,7 +285,10 @@ int sharp_plan_create(sharp_plan* out, int K, int m, int ny, int nx, const int32
     if (params) prm = *params;
     if (!(prm.beta > 0.f && prm.beta <= 1.f)) return fail(SHARP_ERR_INVALID_ARG, "beta = %g outside (0, 1]", prm.beta);
     if (prm.probe_every < 0 || prm.residual_every < 0) return fail(SHARP_ERR_INVALID_ARG, "negative cadence");
-    if (prm.precision != SHARP_PREC_FP32) return fail(SHARP_ERR_INVALID_ARG, "unknown precision %d", prm.precision);
+    if (prm.precision != SHARP_PREC_FP32 && prm.precision != SHARP_PREC_FP16S && prm.precision != SHARP_PREC_BF16X3)
+        return fail(SHARP_ERR_INVALID_ARG, "unknown precision %d", prm.precision);
+    if (prm.precision != SHARP_PREC_FP32 && m != 128)
+        return fail(SHARP_ERR_UNSUPPORTED_SIZE, "tensor-core precision modes need m = 128 (m = %d)", m);
 
     std::vector<int32_t> hpos((size_t)K * 2);
     SHARP_CK(cudaMemcpyAsync(hpos.data(), pos, hpos.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
@@ -321,6 +370,13 @@ int sharp_plan_create(sharp_plan* out, int K, int m, int ny, int nx, const int32
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         SHARP_ALLOC(big_scratch, (size_t)sms * mm)
+    }
+    std::vector<uint16_t> dft;
+    if (prm.precision != SHARP_PREC_FP32) {
+        dft = dft_table(prm.precision, m);
+        if (e == cudaSuccess) e = cudaMalloc(&p.dft_tab, dft.size() * sizeof(uint16_t));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p.dft_tab, dft.data(), dft.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, stream);
     }
 #undef SHARP_ALLOC
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.pos, hpos.data(), hpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice, stream);
@@ -415,7 +471,8 @@ int sharp_fourier_project(sharp_plan plan, const float2* z, const float* amp, fl
     a.zin = z;
     a.zout = out;
     a.amp = amp;
-    SHARP_CK(sharp::launch_frames(sharp::MODE_PROJECT, 0, a, s));
+    if (mixed(p)) SHARP_CK(sharp::launch_mixed(p.prm.precision, sharp::MODE_PROJECT, 0, a, s));
+    else SHARP_CK(sharp::launch_frames(sharp::MODE_PROJECT, 0, a, s));
     if (resid_sq) SHARP_CK(sharp::launch_copy_scaled(p.sums, resid_sq, 1.0, s));
     return SHARP_OK;
 }
@@ -506,7 +563,10 @@ int sharp_raar_step(sharp_plan plan, float2* state_c, float2* psi_y, float2* psi
     sharp::StepInfo info;
     if (int r = sharp::raar_step_prepare(p, state_c, psi_y, psi, amp, iter, &a, &info)) return r;
     SHARP_CK(sharp::raar_step_clear(p, s));
-    SHARP_CK(timed(p, K_FRAME, 1, s, [&] { return sharp::launch_frames(sharp::MODE_RAAR, info.flags, a, s); }));
+    SHARP_CK(timed(p, K_FRAME, 1, s, [&] {
+        return mixed(p) ? sharp::launch_mixed(p.prm.precision, sharp::MODE_RAAR, info.flags, a, s)
+                        : sharp::launch_frames(sharp::MODE_RAAR, info.flags, a, s);
+    }));
     return sharp::raar_step_finish(p, state_c, psi_y, psi, probe, metrics, iter, info, s, true);
 }
 

@@ -122,6 +122,8 @@ int sharp_batch_create(sharp_batch* out, int nscans, const sharp_plan* plans) {
         const sharp_params& pi = plans[i]->p.prm;
         if (pi.probe_every != p0.probe_every || pi.residual_every != p0.residual_every)
             return bfail(SHARP_ERR_INVALID_ARG, "plans of a batch must share probe_every and residual_every");
+        if (pi.precision != SHARP_PREC_FP32)
+            return bfail(SHARP_ERR_INVALID_ARG, "batched scans run in SHARP_PREC_FP32 only");
     }
     sharp_batch b = new sharp_batch_s;
     b->plans.assign(plans, plans + nscans);

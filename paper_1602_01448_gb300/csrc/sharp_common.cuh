@@ -120,6 +120,9 @@ struct Plan {
     int probe_cons_kind;     // SHARP_PROBE_CONSTRAINT_*
     int probe_com;           // centre the probe after each update
     float2* w_tmp;           // m*m scratch probe
+    // tensor-core precision modes: the m x m DFT matrix parts in the operand
+    // layout of the contraction kernels (nullptr in FP32 mode)
+    void* dft_tab;
 };
 
 constexpr int TILE = 32;
@@ -158,6 +161,7 @@ struct FrameArgs {
     int* err;                // device error flag (SHARP_ERR_TIMEOUT on a bounded-wait failure)
     int* counter;            // frame counter of the persistent RAAR pass (zeroed per launch)
     float2* scratch;         // 256^2 frames: one m*m slab per block of the frame kernels
+    const void* dft_tab;     // tensor-core precision modes: DFT matrix parts (raar_mixed.cuh layout)
 };
 
 // compile-time flags of MODE_RAAR
@@ -171,6 +175,13 @@ template <int M>
 inline cudaError_t launch_raar_m(int flags, const FrameArgs& a, cudaStream_t s) {
     return a.wrap ? launch_raar_w<M, 1>(flags, a, s) : launch_raar_w<M, 0>(flags, a, s);
 }
+
+// Tensor-core precision modes (raar_mixed.cuh; m = 128): the RAAR frame pass
+// (MODE_RAAR) and the data projection (MODE_PROJECT) with the frame DFTs as
+// FP16 / BF16x3 contractions.
+template <int PREC>
+cudaError_t launch_mixed_prec(int mode, int flags, const FrameArgs& a, cudaStream_t s);
+cudaError_t launch_mixed(int prec, int mode, int flags, const FrameArgs& a, cudaStream_t s);  // sharp_api.cu
 
 // 256^2 frames (frame256_raar.cu, frame256_ops.cu): the RAAR pass for one
 // scan (bt null) or a batch, and the standalone modes; slabs of m*m scratch,

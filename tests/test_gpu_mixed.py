@@ -1,0 +1,228 @@
+"""GPU parity of the tensor-core precision modes against the FP64 oracle: the
+frame DFTs (Eq. 2) of the data projection (Eq. 7) and of the RAAR step
+(Sec. 2.2) as FP16 (per-frame power-of-two scaling) or BF16 three-term
+contractions with FP32 accumulation, 128 x 128 frames.
+
+Tolerances follow from the operand rounding: FP16 keeps 11 significant bits
+(relative rounding error <= 2^-12 ~ 2.4e-4 per operand, RMS ~1.4e-4), so one
+2D transform (two contractions, each rounding both operands) is off by
+~3e-4 RMS and a projection (two transforms) by ~5e-4: the bound is 3e-3.
+The BF16 split x = hi + lo keeps ~16 bits and drops the lo.lo product
+(~2^-18 each): ~1.2e-5 per projection, bound 5e-5.  A RAAR step compounds the
+error of the state it starts from, so step-level bounds grow with the step
+count."""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+from tests.gpu_util import dev, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"bf16x3": 5e-5, "fp16s": 3e-3}
+MET = {"bf16x3": 2e-3, "fp16s": 3e-2}
+PRECS = ["bf16x3", "fp16s"]
+
+
+def _lib():
+    import paper_1602_01448_gb300 as S
+    return S
+
+
+def _case(seed=0, wrap=False):
+    m = 128
+    rng = np.random.default_rng(seed)
+    ny, nx = m + 75, m + 101
+    if wrap:
+        pos = np.array([[0, 0], [ny - m // 2, nx - 7], [5, nx - m + 40], [ny - 3, 11], [30, 40]], np.int32)
+    else:
+        pos = np.array([[0, 0], [ny - m, nx - m], [0, nx - m], [ny - m, 0], [37, 51], [12, 80]], np.int32)
+    obj = synth.random_object((ny, nx), rng)
+    w = synth.gaussian_probe(m, m / 6.0, rng)
+    return pos, obj, w, (ny, nx)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_mixed_fourier_projection(prec):
+    S = _lib()
+    pos, obj, w, shape = _case()
+    plan = S.Plan(pos, 128, shape, precision=prec)
+    z = synth.random_frames(len(pos), 128, 4)
+    a = synth.random_amplitudes(len(pos), 128, 5)
+    a[1] = 0.0                                   # an all-zero frame of data
+    z[2] = 0.0                                   # |Fz| = 0 everywhere: phase-1 reading
+    z[3] *= 1e-6                                 # a faint frame (the FP16 scaling keeps its precision)
+    out, r = plan.fourier_project(dev(z), dev(a, torch.float32))
+    a32 = a.astype(np.float32).astype(np.float64)
+    ref = O.data_project(z, a32)
+    got = host(out)
+    err = rel_l2(got, ref)
+    print(f"{prec}: P_a relative L2 error {err:.3e}")
+    assert err < TOL[prec]
+    for i in range(len(pos)):
+        if np.any(ref[i] != 0):
+            assert rel_l2(got[i], ref[i]) < TOL[prec], i
+    rr = O.norm(ref - z) ** 2
+    assert abs(r.item() - rr) < 3 * TOL[prec] * rr
+    zt = dev(z)                                  # in place
+    S.sharp_fourier_project(plan.handle, zt, dev(a, torch.float32), zt)
+    assert rel_l2(host(zt), ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_mixed_projection_agrees_with_fp32_path(prec):
+    # the same call on an FP32 plan (an independent FFT implementation) is
+    # within the mixed mode's bound of the mixed result
+    S = _lib()
+    pos, obj, w, shape = _case(seed=1)
+    z = dev(synth.random_frames(len(pos), 128, 6))
+    a = dev(synth.random_amplitudes(len(pos), 128, 7), torch.float32)
+    o32, _ = S.Plan(pos, 128, shape).fourier_project(z, a)
+    omx, _ = S.Plan(pos, 128, shape, precision=prec).fourier_project(z, a)
+    assert rel_l2(host(omx), host(o32)) < TOL[prec]
+
+
+def _noisy_scan(side, step, n_extra, seed, photons=1e5, wrap=False):
+    m = 128
+    rng = np.random.default_rng(seed)
+    ext = (side - 1) * step + m
+    n = ext + n_extra
+    shape = (n, n)
+    obj = synth.random_object(shape, rng)
+    w = synth.gaussian_probe(m, m / 6.0, rng)
+    pos = synth.raster_positions(side, side, step, m, shape, rng, jitter=1)
+    inten = O.forward_amplitudes(obj, w, pos) ** 2
+    a = np.sqrt(synth.poisson_intensities(inten, photons, rng)) if photons else np.sqrt(inten)
+    return obj, w, pos, shape, a.astype(np.float32).astype(np.float64)
+
+
+def _check_metrics(gpu, rec, tol):
+    for k, key in enumerate(("eps_a", "eps_q", "eps_delta")):
+        assert abs(gpu[k] - rec[key]) <= tol * rec[key] + 1e-5, (key, gpu[k], rec[key])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("probe_every", [0, 2])
+def test_mixed_raar_steps_match_oracle(prec, probe_every):
+    S = _lib()
+    obj, w, pos, shape, a = _noisy_scan(4, 24, 37, seed=21 + probe_every, photons=1e6)
+    rng = np.random.default_rng(5)
+    psi0 = synth.random_object(shape, rng, phase_sigma=1.0)
+    w0 = synth.perturb_probe(w, rng, 0.1) if probe_every else w
+    n_steps = 4
+    ref = O.raar_reconstruct(a, pos, shape, w0, psi0, n_steps, beta=0.75, probe_every=probe_every)
+    plan = S.Plan(pos, 128, shape, beta=0.75, probe_every=probe_every, residual_every=1, precision=prec)
+    plan.raar_init(dev(psi0), dev(w0))
+    ta = dev(a, torch.float32)
+    for step_i in range(n_steps):
+        met = host(plan.raar_step(ta)).real
+        _check_metrics(met, ref["history"][step_i], MET[prec])
+        assert abs(met[3] - O.norm(a)) < 1e-5 * O.norm(a)
+    plan.status()
+    D = O.illumination(ref["w"], pos, shape)
+    vis = D > 1e-3 * D.max()
+    err = rel_l2(host(plan.psi), ref["psi"], vis)
+    print(f"{prec} probe_every={probe_every}: object error after {n_steps} steps {err:.3e}")
+    assert err < 2 * n_steps * TOL[prec]
+    if probe_every:
+        assert rel_l2(host(plan.probe), ref["w"]) < 2 * n_steps * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_mixed_raar_wrapped_raster_matches_oracle(prec):
+    # periodic boundary (the 40 x 40 raster geometry at a smaller size)
+    S = _lib()
+    m = 128
+    rng = np.random.default_rng(31)
+    shape = (192, 192)
+    obj = synth.random_object(shape, rng)
+    w = synth.gaussian_probe(m, m / 6.0, rng)
+    pos = np.array([[i * 40 % 192, j * 40 % 192] for i in range(5) for j in range(5)], np.int32)
+    a = O.forward_amplitudes(obj, w, pos, True)
+    a = np.abs(a * (1 + 0.05 * rng.standard_normal(a.shape))).astype(np.float32).astype(np.float64)
+    psi0 = synth.random_object(shape, rng, phase_sigma=1.0)
+    ref = O.raar_reconstruct(a, pos, shape, w, psi0, 3, beta=0.75, wrap=True)
+    plan = S.Plan(pos, m, shape, wrap=True, residual_every=1, precision=prec)
+    plan.raar_init(dev(psi0), dev(w))
+    ta = dev(a, torch.float32)
+    for step_i in range(3):
+        met = host(plan.raar_step(ta)).real
+        _check_metrics(met, ref["history"][step_i], MET[prec])
+    assert rel_l2(host(plan.psi), ref["psi"]) < 6 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_mixed_exact_data_stays_at_the_fixed_point(prec):
+    # exact frames of a known object and probe are a fixed point of RAAR
+    # (Sec. 2.2); the mixed transforms perturb it only by their rounding
+    S = _lib()
+    obj, w, pos, shape, a = _noisy_scan(4, 24, 16, seed=5, photons=None)
+    plan = S.Plan(pos, 128, shape, precision=prec)
+    plan.raar_init(dev(obj), dev(w))
+    ta = dev(a, torch.float32)
+    for _ in range(5):
+        met = host(plan.raar_step(ta)).real
+    assert met[0] < TOL[prec] and met[1] < TOL[prec], met
+    D = O.illumination(w, pos, shape)
+    vis = D > 1e-3 * D.max()
+    assert rel_l2(host(plan.psi), obj, vis) < TOL[prec]
+
+
+@functools.lru_cache(maxsize=1)
+def _convergence_case():
+    m = 128
+    rng = np.random.default_rng(41)
+    shape = (5 * 22 + m + 24,) * 2
+    obj = synth.random_object(shape, rng)
+    w = synth.aperture_probe(m, 32, 0.5)
+    pos = synth.raster_positions(6, 6, 22, m, shape, rng, jitter=1)
+    a = O.forward_amplitudes(obj, w, pos).astype(np.float32).astype(np.float64)
+    psi0 = np.ones(shape, complex)
+    ref = O.raar_reconstruct(a, pos, shape, w, psi0, 100, psi_true=obj, record_metrics=False)
+    return m, shape, obj, w, pos, a, psi0, [h["eps_0"] for h in ref["history"]]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_mixed_nrmse_trajectory_against_oracle(prec):
+    # noiseless 6 x 6 raster of 128^2 frames, known probe, 100 iterations:
+    # eps_0 (Eq. 14) of the mixed-precision reconstruction tracks the FP64
+    # oracle's within 1.02x while the oracle is above the mode's floor
+    # (1e-4 for BF16x3, 3e-3 for FP16), and ends below the floor x 3
+    S = _lib()
+    m, shape, obj, w, pos, a, psi0, e_ref = _convergence_case()
+    n_it = len(e_ref)
+    plan = S.Plan(pos, m, shape, residual_every=0, precision=prec)
+    plan.raar_init(dev(psi0), dev(w))
+    ta = dev(a, torch.float32)
+    tobj, tw = dev(obj), dev(w)
+    floor = {"bf16x3": 1e-4, "fp16s": 3e-3}[prec]
+    ratios, e_gpu = {}, None
+    for it in range(1, n_it + 1):
+        plan.raar_step(ta, metrics=False)
+        if it % 10 == 0:
+            e_gpu = plan.solution_error(plan.psi, tobj, tw)[0].item()
+            ratios[it] = (e_gpu, e_ref[it - 1])
+    print(prec, "eps_0 (GPU, oracle) by iteration:", {k: (f"{g:.3e}", f"{r:.3e}") for k, (g, r) in ratios.items()})
+    for it, (g, r) in ratios.items():
+        if r > floor:
+            assert g <= 1.02 * r, (it, g, r)
+    assert e_gpu < max(3 * floor, 1.02 * e_ref[-1])
+
+
+def test_mixed_modes_reject_other_frame_sizes_and_batches():
+    S = _lib()
+    pos, obj, w, shape = _case()
+    for m in (64, 256):
+        with pytest.raises(S.SharpError) as ei:
+            S.Plan(np.zeros((2, 2), np.int32), m, (m + 8, m + 8), precision="fp16s")
+        assert "UNSUPPORTED_SIZE" in str(ei.value)
+    with pytest.raises(S.SharpError):
+        S.Plan(pos, 128, shape, precision=7)
+    plan = S.Plan(pos, 128, shape, precision="bf16x3")
+    plan.raar_init(dev(obj), dev(w))
+    with pytest.raises(S.SharpError):
+        S.Batch([plan], [dev(np.ones((len(pos), 128, 128)), torch.float32)])
