@@ -134,6 +134,16 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+def measured_peak_tensor():
+    """Measured dense BF16 tensor rate (TFLOP/s, burst) of this pool's GPUs;
+    FP16 has the same nominal dense rate."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
 def slowest_rank_ms(ms: float, world: int, device=None) -> float:
     """Max over ranks of a per-rank time (the job is as slow as its slowest
     replica); identity for a single process."""
@@ -227,6 +237,54 @@ def run_reference(args, rank):
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def time_mixed(S, scan, amp, psi0, w0, prec, steps, warmup, world, dev):
+    """The same RAAR steps with the frame DFTs as tensor-core contractions
+    (precision `prec`, 128^2 frames): throughput, frame-kernel time, its HBM
+    fraction (20 m^2 B per frame) and its tensor-pipe rate (4 complex
+    128 x 128 x 128 products per frame = 16 real ones, 2 m^3 flops each; the
+    BF16 three-term split issues each real product three times)."""
+    import torch
+    K, m = scan.K, scan.m
+    plan = S.Plan(scan.pos, m, scan.shape, beta=0.75, probe_every=scan.probe_every,
+                  residual_every=RESIDUAL_EVERY, device=dev, precision=prec)
+    plan.raar_init(psi0, w0)
+    for _ in range(warmup):
+        plan.raar_step(amp)
+    torch.cuda.synchronize()
+    S.sharp_plan_set_profiling(plan.handle, True)
+    S.sharp_plan_kernel_times(plan.handle)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.raar_step(amp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_total = slowest_rank_ms(e0.elapsed_time(e1), world, dev)
+    kt = S.sharp_plan_kernel_times(plan.handle)
+    S.sharp_plan_set_profiling(plan.handle, False)
+    plan.status()
+    frame_ms, frame_n = kt["frame"]
+    t_frame = frame_ms / max(frame_n, 1) / 1000.0
+    peak_hbm, _ = measured_peak_hbm()
+    terms = 3 if prec == "bf16x3" else 1
+    flops = 16 * 2.0 * m ** 3 * terms * K
+    peak_tc = measured_peak_tensor()
+    met = plan.metrics.cpu().numpy().tolist()
+    launches = sum(n for _, n in kt.values())
+    out = {"precision": prec, "value": job_throughput(K, steps, world, ms_total), "unit": UNIT,
+           "ms_per_step": ms_total / steps, "frame_kernel_ms": t_frame * 1000.0,
+           "hbm": {"achieved": 20.0 * m * m * K / t_frame / 1e9, "peak": peak_hbm, "unit": "GB/s",
+                   "frac": 20.0 * m * m * K / t_frame / 1e9 / peak_hbm},
+           "tensor": {"achieved": flops / t_frame / 1e12, "peak": peak_tc, "unit": "TFLOP/s",
+                      "frac": flops / t_frame / 1e12 / peak_tc if peak_tc else None,
+                      "flops_per_launch": flops, "terms": terms},
+           "gpu_launches": launches, "last_metrics": {"eps_a": met[0], "eps_q": met[1]}}
+    plan.close()
+    return out
 
 
 def run_ours(args, rank, world):
@@ -349,6 +407,11 @@ def run_ours(args, rank, world):
     e2e_ms = f0.elapsed_time(f1) / e2e_steps
     e2e_ms = slowest_rank_ms(e2e_ms, world, dev)
 
+    mixed = []
+    if m == 128 and not args.no_mixed:
+        for prec in ("fp16s", "bf16x3"):
+            mixed.append(time_mixed(S, scan, amp, psi0, w0, prec, args.steps, args.warmup, world, dev))
+
     if rank != 0:
         return
     cpu = None
@@ -382,6 +445,9 @@ def run_ours(args, rank, world):
         "gpu_launches": launches,
         "clocks": clocks,
         "last_metrics": {"eps_a": metrics[0], "eps_q": metrics[1]},
+        # the same workload with the frame DFTs as tensor-core contractions
+        # (FP16 per-frame scaled; BF16 three-term), timed after the FP32 run
+        "mixed": mixed,
     }
     print(json.dumps(out), flush=True)
 
@@ -511,6 +577,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the tensor-core precision modes (128^2 frames)")
     ap.add_argument("--workload", default="fermat", choices=["fermat", "raster256", "batch", "batch-small"])
     ap.add_argument("--frames", type=int, default=None,
                     help="frames of the scan (default: the workload's; fewer for small ncu captures; "

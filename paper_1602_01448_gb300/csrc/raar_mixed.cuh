@@ -17,8 +17,7 @@
 //   C(r + x_i) += conj(w) c_i
 // and, as the standalone data projection P_a of Eq. 7, out = F* (a Z/|Z|) F*^T.
 //
-// One frame per block at a time (persistent, one block per SM).  A 2D
-// transform is two contractions with the roles of the frame's indices
+// A 2D transform is two contractions with the roles of the frame's indices
 // swapped, so every intermediate leaves tensor memory already in the layout
 // the next contraction reads:
 //   stage 1: D1[k1][n2] = sum_n1 F[k1][n1]  z[n1][n2]      (B rows = n2)
@@ -33,12 +32,24 @@
 // D_i = A_r B_i +- A_i B_r (the sign of the A_i terms through the
 // instruction's negate-A bit: forward F, inverse F*).
 //
-// Thread t of the 512 (16 warps) owns TMEM lane r = 32 (w % 4) + lane and the
-// columns 64 j + 16 (w / 4) + [0, 16) for j = 0, 1; in frame coordinates that
-// is one column index n2 = r (coalesced global accesses across a warp) and 32
-// row indices.  TMEM holds two 256-column regions P and Q (real part in
-// columns 0-127 of a region, imaginary part in 128-255); stages alternate
-// between them (z in P -> D1 in Q -> D2 in P -> D3 in Q -> D4 in P).
+// Frame groups.  A block of 512 threads (16 warps, one block per SM) runs NG
+// frame groups, each an independent pipeline over its own frames with its own
+// TMEM columns, B buffer, mbarrier and named barrier; the DFT matrix is
+// shared.  Thread t of a group owns TMEM lane r = 32 (w % 4) + lane and, in
+// each of the two K-chunks j of 64 columns, the CW columns
+// 64 j + CW (w_g / 4) + [0, CW); in frame coordinates that is one column
+// index n2 = r (coalesced global accesses across a warp) and 2 CW row
+// indices.
+//  - FP16S: two groups of 256 threads (CW = 32).  A stage converts all of its
+//    input (both K-chunks, 64 KB of B) before it issues any MMA, so the
+//    result can overwrite the input in place: a frame needs 256 TMEM columns
+//    (real part in 0-127, imaginary in 128-255) and the two groups fill all
+//    512.  While one group waits on memory (gathers, amplitudes, scatter) the
+//    other group's contractions run.
+//  - BF16X3: one group of 512 threads (CW = 16).  Its operands are twice as
+//    large (hi and lo parts), so B holds one K-chunk at a time and a stage
+//    alternates between two 256-column regions P and Q
+//    (z in P -> D1 in Q -> D2 in P -> D3 in Q -> D4 in P).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -54,35 +65,41 @@ struct MixGeo {
     static constexpr int M = 128;
     static constexpr int NT = 512;
     static constexpr bool F16 = PREC == SHARP_PREC_FP16S;
+    static constexpr int NG = F16 ? 2 : 1;              // frame groups per block
+    static constexpr int GT = NT / NG;                  // threads per group
+    static constexpr int GW = GT / 32;                  // warps per group
+    static constexpr int CW = 64 / (GW / 4);            // columns per thread per K-chunk
     static constexpr int NPART = F16 ? 2 : 4;           // operand parts: {re, im} or {re_hi, re_lo, im_hi, im_lo}
-    static constexpr int NBUF = F16 ? 2 : 1;            // K-chunk buffers of B (two K-chunks of 64 per stage)
+    static constexpr int NBUF = F16 ? 2 : 1;            // K-chunks of 64 held in B at once
     static constexpr int A_PART = M * M * 2;            // 32 KB: one 128 x 128 16-bit matrix
     static constexpr int B_PART = M * 64 * 2;           // 16 KB: 128 rows x one K-chunk of 64
     static constexpr int A_BYTES = NPART * A_PART;
     static constexpr int B_SLOT = NPART * B_PART;
-    static constexpr int B_BYTES = NBUF * B_SLOT;
-    // Unused tail: keeps any operand read of a descriptor within the block's
-    // shared memory.
-    static constexpr int GUARD = 32768;
-    static constexpr int SMEM = A_BYTES + B_BYTES + GUARD + 128;
+    static constexpr int B_GROUP = NBUF * B_SLOT;
+    static constexpr int SMEM = A_BYTES + NG * B_GROUP + 128;
     static constexpr uint32_t LBO = 16 * 128;           // K-adjacent core matrices (16 row groups of 128 B)
     static constexpr uint32_t SBO = 128;                // row-group-adjacent core matrices
-    static constexpr uint32_t T_P = 0, T_Q = 256;       // TMEM regions
     static_assert(SMEM <= 232448, "shared memory of one block");
     static_assert(SMEM > 232448 / 2, "one block per SM: the kernel allocates all 512 TMEM columns");
+    static_assert(CW % 16 == 0, "TMEM accesses of 16 columns");
 };
 
-// Largest |component| of the block (all threads receive it).
-__device__ __forceinline__ float mix_block_max(float v, float* s_max) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float m = s_max[0];
-#pragma unroll
-    for (int k = 1; k < 16; ++k) m = fmaxf(m, s_max[k]);
-    return m;
+// ------------------------------------------------------------ group sync
+__device__ __forceinline__ void group_bar(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// Barrier of the group that also ANDs a predicate over its threads.
+__device__ __forceinline__ bool group_and(bool v, int id, int count) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.b32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\t"
+        "selp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((int)v), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
 }
 
 // Power of two 2^e with mx 2^e in [2^14, 2^15) (1 for 0, Inf or NaN).
@@ -109,53 +126,79 @@ __device__ __forceinline__ uint32_t pack_b2(__nv_bfloat16 x, __nv_bfloat16 y) {
     h.y = y;
     return *reinterpret_cast<const uint32_t*>(&h);
 }
+// hi and lo BF16 parts of (x, y), packed
+__device__ __forceinline__ void split_b2(float x, float y, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat16 hx = __float2bfloat16_rn(x), hy = __float2bfloat16_rn(y);
+    hi = pack_b2(hx, hy);
+    lo = pack_b2(__float2bfloat16_rn(x - __bfloat162float(hx)), __float2bfloat16_rn(y - __bfloat162float(hy)));
+}
 
-// Write this thread's 16 K-values (row r, K-local 16 h .. 16 h + 15 of a
-// K-chunk) of the real and imaginary planes, times g, into the B buffer `sb`.
+// Per-thread state of a frame group.
+struct MixCtx {
+    uint32_t sA;           // shared address of the DFT matrix parts
+    uint32_t sB;           // this group's B buffer
+    uint32_t tbase;        // TMEM base (lane 0, column 0)
+    uint32_t tl;           // TMEM address of this warp's lane quarter
+    int r, h;              // TMEM lane (frame index owned) and column group
+    int bar_id;            // named barrier of the group
+    bool leader;           // issues the group's MMAs
+    uint64_t* bar;         // MMA completion of the group
+    float* s_max;          // GW floats
+    unsigned phase;
+};
+
+// Largest value over the group (all its threads receive it).
 template <int PREC>
-__device__ __forceinline__ void mix_put(uint32_t sb, int r, int h, const float (&re)[16], const float (&im)[16],
-                                        float g) {
+__device__ __forceinline__ float mix_group_max(const MixCtx& x, float v) {
     using G = MixGeo<PREC>;
-    const uint32_t off0 = (uint32_t)(((2 * h) * 16 + (r >> 3)) * 128 + (r & 7) * 16);   // core matrix (r/8, 2h)
-    const uint32_t off1 = off0 + G::LBO;                                                 // (r/8, 2h + 1)
-    if constexpr (G::F16) {
-        uint32_t pr[8], pi[8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            pr[t] = pack_h2(re[2 * t] * g, re[2 * t + 1] * g);
-            pi[t] = pack_h2(im[2 * t] * g, im[2 * t + 1] * g);
-        }
-        sts128(sb + off0, pr[0], pr[1], pr[2], pr[3]);
-        sts128(sb + off1, pr[4], pr[5], pr[6], pr[7]);
-        sts128(sb + G::B_PART + off0, pi[0], pi[1], pi[2], pi[3]);
-        sts128(sb + G::B_PART + off1, pi[4], pi[5], pi[6], pi[7]);
-    } else {
-        uint32_t rh[8], rl[8], ih[8], il[8];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    group_bar(x.bar_id, G::GT);
+    if ((threadIdx.x & 31) == 0) x.s_max[(threadIdx.x % G::GT) >> 5] = v;
+    group_bar(x.bar_id, G::GT);
+    float m = x.s_max[0];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            __nv_bfloat16 h0 = __float2bfloat16_rn(re[2 * t]), h1 = __float2bfloat16_rn(re[2 * t + 1]);
-            rh[t] = pack_b2(h0, h1);
-            rl[t] = pack_b2(__float2bfloat16_rn(re[2 * t] - __bfloat162float(h0)),
-                            __float2bfloat16_rn(re[2 * t + 1] - __bfloat162float(h1)));
-            h0 = __float2bfloat16_rn(im[2 * t]);
-            h1 = __float2bfloat16_rn(im[2 * t + 1]);
-            ih[t] = pack_b2(h0, h1);
-            il[t] = pack_b2(__float2bfloat16_rn(im[2 * t] - __bfloat162float(h0)),
-                            __float2bfloat16_rn(im[2 * t + 1] - __bfloat162float(h1)));
+    for (int k = 1; k < G::GW; ++k) m = fmaxf(m, x.s_max[k]);
+    return m;
+}
+
+// Columns of this thread in K-chunk j.
+template <int PREC>
+__device__ __forceinline__ int mix_col(int j, int h) { return 64 * j + MixGeo<PREC>::CW * h; }
+
+// Write 16 K-values of this thread (row r of B, K-groups kg and kg + 1 of a
+// K-chunk) of the real and imaginary planes, times g, into B buffer sb.
+template <int PREC>
+__device__ __forceinline__ void mix_put16(uint32_t sb, int r, int kg, const float (&re)[16], const float (&im)[16],
+                                          float g) {
+    using G = MixGeo<PREC>;
+    const uint32_t base = (uint32_t)((kg * 16 + (r >> 3)) * 128 + (r & 7) * 16);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const uint32_t off = base + u * G::LBO;
+        const float* pr = re + 8 * u;
+        const float* pi = im + 8 * u;
+        if constexpr (G::F16) {
+            sts128(sb + off, pack_h2(pr[0] * g, pr[1] * g), pack_h2(pr[2] * g, pr[3] * g),
+                   pack_h2(pr[4] * g, pr[5] * g), pack_h2(pr[6] * g, pr[7] * g));
+            sts128(sb + G::B_PART + off, pack_h2(pi[0] * g, pi[1] * g), pack_h2(pi[2] * g, pi[3] * g),
+                   pack_h2(pi[4] * g, pi[5] * g), pack_h2(pi[6] * g, pi[7] * g));
+        } else {
+            uint32_t h4[4], l4[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) split_b2(pr[2 * t] * g, pr[2 * t + 1] * g, h4[t], l4[t]);
+            sts128(sb + off, h4[0], h4[1], h4[2], h4[3]);
+            sts128(sb + G::B_PART + off, l4[0], l4[1], l4[2], l4[3]);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) split_b2(pi[2 * t] * g, pi[2 * t + 1] * g, h4[t], l4[t]);
+            sts128(sb + 2 * G::B_PART + off, h4[0], h4[1], h4[2], h4[3]);
+            sts128(sb + 3 * G::B_PART + off, l4[0], l4[1], l4[2], l4[3]);
         }
-        sts128(sb + off0, rh[0], rh[1], rh[2], rh[3]);
-        sts128(sb + off1, rh[4], rh[5], rh[6], rh[7]);
-        sts128(sb + G::B_PART + off0, rl[0], rl[1], rl[2], rl[3]);
-        sts128(sb + G::B_PART + off1, rl[4], rl[5], rl[6], rl[7]);
-        sts128(sb + 2 * G::B_PART + off0, ih[0], ih[1], ih[2], ih[3]);
-        sts128(sb + 2 * G::B_PART + off1, ih[4], ih[5], ih[6], ih[7]);
-        sts128(sb + 3 * G::B_PART + off0, il[0], il[1], il[2], il[3]);
-        sts128(sb + 3 * G::B_PART + off1, il[4], il[5], il[6], il[7]);
     }
 }
 
-// MMAs of K-chunk j of one stage (thread 0): D (columns d, d + 128) +=
-// F(or F*)[:, 64 j .. 64 j + 63] . B(chunk)^T.
+// MMAs of K-chunk j of one stage (the group leader): D (columns d, d + 128)
+// (+)= F(or F*)[:, 64 j .. 64 j + 63] . B(chunk in sb)^T.
 template <int PREC>
 __device__ __forceinline__ void mix_issue(uint32_t sA, uint32_t sb, uint32_t d, int j, bool inverse) {
     using G = MixGeo<PREC>;
@@ -190,63 +233,84 @@ __device__ __forceinline__ void mix_issue(uint32_t sA, uint32_t sb, uint32_t d, 
     }
 }
 
-// Shared state of one block.
-struct MixCtx {
-    uint32_t sA, sB;       // shared addresses of the DFT matrix parts and the B buffers
-    uint32_t tbase;        // TMEM base (lane 0, column 0)
-    uint32_t tl;           // TMEM address of this warp's lane quarter
-    int r, h;              // TMEM lane (frame index owned) and column group
-    uint64_t* bar;         // MMA completion
-    float* s_max;
-    unsigned phase;
-};
+// Convert this thread's CW columns of K-chunk j of region `src`, times g,
+// into B buffer sb (16 columns at a time).
+template <int PREC>
+__device__ __forceinline__ void mix_convert(const MixCtx& x, uint32_t src, int j, uint32_t sb, float g) {
+    using G = MixGeo<PREC>;
+    const int c = mix_col<PREC>(j, x.h);
+#pragma unroll
+    for (int s = 0; s < G::CW / 16; ++s) {
+        float re[16], im[16];
+        tmem_ld16x2(x.tl + src + c + 16 * s, x.tl + src + 128 + c + 16 * s, re, im);
+        mix_put16<PREC>(sb, x.r, (G::CW / 8) * x.h + 2 * s, re, im, g);
+    }
+}
 
-// Columns of this thread in K-chunk j.
-__device__ __forceinline__ int mix_col(int j, int h) { return 64 * j + 16 * h; }
-
-// Largest component of region `src` over the block.
+// Largest component of region `src` over the group.
+template <int PREC>
 __device__ __forceinline__ float mix_region_max(const MixCtx& x, uint32_t src) {
+    using G = MixGeo<PREC>;
     float mx = 0.f;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-        float re[16], im[16];
-        const uint32_t c = (uint32_t)mix_col(j, x.h);
-        tmem_ld16x2(x.tl + src + c, x.tl + src + 128 + c, re, im);
+        const int c = mix_col<PREC>(j, x.h);
 #pragma unroll
-        for (int t = 0; t < 16; ++t) mx = fmaxf(mx, fmaxf(fabsf(re[t]), fabsf(im[t])));
+        for (int s = 0; s < G::CW / 16; ++s) {
+            float re[16], im[16];
+            tmem_ld16x2(x.tl + src + c + 16 * s, x.tl + src + 128 + c + 16 * s, re, im);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) mx = fmaxf(mx, fmaxf(fabsf(re[t]), fabsf(im[t])));
+        }
     }
-    return mix_block_max(mx, x.s_max);
+    return mix_group_max<PREC>(x, mx);
+}
+
+// Wait (bounded) for the group's MMAs; false if the wait gave up.
+template <int PREC>
+__device__ __forceinline__ bool mix_wait(MixCtx& x) {
+    const bool ok = group_and(mbar_wait(x.bar, x.phase), x.bar_id, MixGeo<PREC>::GT);
+    if (!ok) return false;
+    x.phase ^= 1u;
+    tc_fence_after();
+    return true;
 }
 
 // One contraction stage: region dst = F(or F*) . (g * region src)^T in the
-// stage layout above.  False if an MMA completion wait gave up.
+// stage layout above (dst == src for FP16S: the whole input is in shared
+// memory before the first MMA).  False if an MMA completion wait gave up.
 template <int PREC>
 __device__ __forceinline__ bool mix_stage(MixCtx& x, uint32_t src, uint32_t dst, bool inverse, float g) {
     using G = MixGeo<PREC>;
+    if constexpr (G::NBUF == 2) {
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const uint32_t sb = x.sB + (uint32_t)((G::NBUF == 2 ? j : 0) * G::B_SLOT);
-        float re[16], im[16];
-        const uint32_t c = (uint32_t)mix_col(j, x.h);
-        tmem_ld16x2(x.tl + src + c, x.tl + src + 128 + c, re, im);
-        mix_put<PREC>(sb, x.r, x.h, re, im, g);
+        for (int j = 0; j < 2; ++j) mix_convert<PREC>(x, src, j, x.sB + j * G::B_SLOT, g);
         fence_proxy_async_smem();   // generic-proxy writes -> tensor-core (async proxy) reads
         tc_fence_before();
-        __syncthreads();
-        const bool commit = (G::NBUF == 1) || (j == 1);
-        if (threadIdx.x == 0) {
+        group_bar(x.bar_id, G::GT);
+        if (x.leader) {
             tc_fence_after();
-            mix_issue<PREC>(x.sA, sb, x.tbase + dst, j, inverse);
-            if (commit) mma_commit(x.bar);
+            mix_issue<PREC>(x.sA, x.sB, x.tbase + dst, 0, inverse);
+            mix_issue<PREC>(x.sA, x.sB + G::B_SLOT, x.tbase + dst, 1, inverse);
+            mma_commit(x.bar);
         }
-        if (commit) {
-            const bool ok = __syncthreads_and(mbar_wait(x.bar, x.phase));
-            if (!ok) return false;
-            x.phase ^= 1u;
-            tc_fence_after();
+        return mix_wait<PREC>(x);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            mix_convert<PREC>(x, src, j, x.sB, g);
+            fence_proxy_async_smem();
+            tc_fence_before();
+            group_bar(x.bar_id, G::GT);
+            if (x.leader) {
+                tc_fence_after();
+                mix_issue<PREC>(x.sA, x.sB, x.tbase + dst, j, inverse);
+                mma_commit(x.bar);
+            }
+            if (!mix_wait<PREC>(x)) return false;
         }
+        return true;
     }
-    return true;
 }
 
 template <int PREC, int MODE, int FLAGS, int WRAP>
@@ -254,33 +318,37 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     using G = MixGeo<PREC>;
     constexpr int M = 128;
     constexpr int MM = M * M;
+    constexpr int CW = G::CW;
     constexpr bool RAAR = MODE == MODE_RAAR;
     extern __shared__ __align__(128) unsigned char mix_smem[];
     __shared__ FrameArgs a;
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bars[G::NG];
     __shared__ uint32_t s_tmem;
     __shared__ float s_max[16];
     __shared__ float red[32 * 5];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grp = warp / G::GW;          // frame group
+    const int wg = warp % G::GW;           // warp within the group
 
     MixCtx x;
     x.sA = (smem_addr(mix_smem) + 127u) & ~127u;
-    x.sB = x.sA + G::A_BYTES;
+    x.sB = x.sA + G::A_BYTES + grp * G::B_GROUP;
     x.r = 32 * (warp & 3) + lane;
-    x.h = warp >> 2;
-    x.bar = &bar;
-    x.s_max = s_max;
+    x.h = wg >> 2;
+    x.bar_id = 1 + grp;
+    x.leader = (tid % G::GT) == 0;
+    x.bar = &bars[grp];
+    x.s_max = s_max + grp * G::GW;
     x.phase = 0;
 
     {   // DFT matrix parts, already in the operand layout, into shared memory
         const uint4* src = reinterpret_cast<const uint4*>(ap.dft_tab);
-        unsigned char* dst = mix_smem + (x.sA - smem_addr(mix_smem));
-        for (int k = tid; k < G::A_BYTES / 16; k += G::NT)
-            reinterpret_cast<uint4*>(dst)[k] = __ldg(src + k);
+        uint4* dst = reinterpret_cast<uint4*>(mix_smem + (x.sA - smem_addr(mix_smem)));
+        for (int k = tid; k < G::A_BYTES / 16; k += G::NT) dst[k] = __ldg(src + k);
     }
     if (tid == 0) {
         a = ap;
-        mbar_init(&bar, 1);
+        for (int k = 0; k < G::NG; ++k) mbar_init(&bars[k], 1);
         mbar_fence_init();
     }
     if (warp == 0) {
@@ -293,6 +361,10 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     tc_fence_after();
     x.tbase = s_tmem;
     x.tl = x.tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+    // TMEM regions: FP16S works in place in the group's 256 columns; BF16X3
+    // alternates between P = 0 and Q = 256
+    const uint32_t RA = G::F16 ? 256u * grp : 0u;
+    const uint32_t RB = G::F16 ? RA : 256u;
 
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
@@ -302,19 +374,19 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     bool ok = true;
 
-    for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
+    for (int i = blockIdx.x * G::NG + grp; i < a.K; i += gridDim.x * G::NG) {
         const size_t fo = (size_t)i * MM;
-        if (tid == 0) bulk_prefetch_l2(a.amp + fo, (unsigned)(MM * sizeof(float)));
+        if (x.leader) bulk_prefetch_l2(a.amp + fo, (unsigned)(MM * sizeof(float)));
         const int py = RAAR ? a.pos[2 * i] : 0;
         const int px = RAAR ? a.pos[2 * i + 1] : 0;
 
-        // ------------------------------------------------ load: z into P
+        // ------------------------------------------------ load: z into RA
         float mx = 0.f;
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-                const int y0 = mix_col(j, x.h) + 8 * hh;
+#pragma unroll 1
+            for (int hh = 0; hh < CW / 8; ++hh) {
+                const int y0 = mix_col<PREC>(j, x.h) + 8 * hh;
                 float zr[8], zi[8];
                 if constexpr (RAAR) {
                     float2 cv[8], wf[8], yv[8], wp[8], pv[8], ev[8];
@@ -362,113 +434,118 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                 }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) mx = fmaxf(mx, fmaxf(fabsf(zr[k]), fabsf(zi[k])));
-                tmem_st8x2(x.tl + G::T_P + y0, x.tl + G::T_P + 128 + y0, zr, zi);
+                tmem_st8x2(x.tl + RA + y0, x.tl + RA + 128 + y0, zr, zi);
             }
         }
         tmem_wait_st();
         float g0 = 1.f, g1 = 1.f, g2 = 1.f, g3 = 1.f;
-        if constexpr (G::F16) g0 = mix_pow2_scale(mix_block_max(mx, s_max));
+        if constexpr (G::F16) g0 = mix_pow2_scale(mix_group_max<PREC>(x, mx));
 
         // ------------------------------------------------ forward transform
-        ok = mix_stage<PREC>(x, G::T_P, G::T_Q, false, g0);
+        ok = mix_stage<PREC>(x, RA, RB, false, g0);
         if (!ok) break;
-        if constexpr (G::F16) g1 = mix_pow2_scale(mix_region_max(x, G::T_Q));
-        ok = mix_stage<PREC>(x, G::T_Q, G::T_P, false, g1);
+        if constexpr (G::F16) g1 = mix_pow2_scale(mix_region_max<PREC>(x, RB));
+        ok = mix_stage<PREC>(x, RB, RA, false, g1);
         if (!ok) break;
 
-        // ------------------------------------------------ Fourier step on P
+        // ------------------------------------------------ Fourier step on RA
         {
             const float inv = 1.f / (g0 * g1);   // exact: powers of two
             float um = 0.f;
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const int k0 = mix_col(j, x.h);
-                float re[16], im[16];
-                tmem_ld16x2(x.tl + G::T_P + k0, x.tl + G::T_P + 128 + k0, re, im);
-                float av[16];
 #pragma unroll
-                for (int t = 0; t < 16; ++t) av[t] = __ldcs(a.amp + fo + (size_t)(k0 + t) * M + xcol);
-                float ur[16], ui[16];
+                for (int s = 0; s < CW / 16; ++s) {
+                    const int k0 = mix_col<PREC>(j, x.h) + 16 * s;
+                    float re[16], im[16];
+                    tmem_ld16x2(x.tl + RA + k0, x.tl + RA + 128 + k0, re, im);
+                    float av[16];
 #pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    const float X = re[t] * inv, Y = im[t] * inv;
-                    const float m2 = fmaf(X, X, Y * Y);
-                    const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
-                    const float d = av[t] - m2 * rs;
-                    acc[0] += d * d;
-                    acc[1] += av[t] * av[t];
-                    if (m2 > 0.f) {
-                        const float f = fmaf(cp * av[t], rs, b);
-                        ur[t] = X * f;
-                        ui[t] = Y * f;
-                    } else {
-                        ur[t] = cp * av[t];
-                        ui[t] = 0.f;
+                    for (int t = 0; t < 16; ++t) av[t] = __ldcs(a.amp + fo + (size_t)(k0 + t) * M + xcol);
+                    float ur[16], ui[16];
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        const float X = re[t] * inv, Y = im[t] * inv;
+                        const float m2 = fmaf(X, X, Y * Y);
+                        const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
+                        const float d = av[t] - m2 * rs;
+                        acc[0] += d * d;
+                        acc[1] += av[t] * av[t];
+                        if (m2 > 0.f) {
+                            const float f = fmaf(cp * av[t], rs, b);
+                            ur[t] = X * f;
+                            ui[t] = Y * f;
+                        } else {
+                            ur[t] = cp * av[t];
+                            ui[t] = 0.f;
+                        }
+                        um = fmaxf(um, fmaxf(fabsf(ur[t]), fabsf(ui[t])));
                     }
-                    um = fmaxf(um, fmaxf(fabsf(ur[t]), fabsf(ui[t])));
+                    float r8[8], i8[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) { r8[t] = ur[t]; i8[t] = ui[t]; }
+                    tmem_st8x2(x.tl + RA + k0, x.tl + RA + 128 + k0, r8, i8);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) { r8[t] = ur[8 + t]; i8[t] = ui[8 + t]; }
+                    tmem_st8x2(x.tl + RA + k0 + 8, x.tl + RA + 128 + k0 + 8, r8, i8);
                 }
-                float r8[8], i8[8];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) { r8[t] = ur[t]; i8[t] = ui[t]; }
-                tmem_st8x2(x.tl + G::T_P + k0, x.tl + G::T_P + 128 + k0, r8, i8);
-#pragma unroll
-                for (int t = 0; t < 8; ++t) { r8[t] = ur[8 + t]; i8[t] = ui[8 + t]; }
-                tmem_st8x2(x.tl + G::T_P + k0 + 8, x.tl + G::T_P + 128 + k0 + 8, r8, i8);
             }
             tmem_wait_st();
-            if constexpr (G::F16) g2 = mix_pow2_scale(mix_block_max(um, s_max));
+            if constexpr (G::F16) g2 = mix_pow2_scale(mix_group_max<PREC>(x, um));
         }
 
         // ------------------------------------------------ inverse transform
-        ok = mix_stage<PREC>(x, G::T_P, G::T_Q, true, g2);
+        ok = mix_stage<PREC>(x, RA, RB, true, g2);
         if (!ok) break;
-        if constexpr (G::F16) g3 = mix_pow2_scale(mix_region_max(x, G::T_Q));
-        ok = mix_stage<PREC>(x, G::T_Q, G::T_P, true, g3);
+        if constexpr (G::F16) g3 = mix_pow2_scale(mix_region_max<PREC>(x, RB));
+        ok = mix_stage<PREC>(x, RB, RA, true, g3);
         if (!ok) break;
 
-        // ------------------------------------------------ epilogue from P
+        // ------------------------------------------------ epilogue from RA
         {
             const float inv = 1.f / (g2 * g3);
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const int y0 = mix_col(j, x.h);
-                float re[16], im[16];
-                tmem_ld16x2(x.tl + G::T_P + y0, x.tl + G::T_P + 128 + y0, re, im);
-                if constexpr (RAAR) {
 #pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        float2 wp[8];
+                for (int s = 0; s < CW / 16; ++s) {
+                    const int y0 = mix_col<PREC>(j, x.h) + 16 * s;
+                    float re[16], im[16];
+                    tmem_ld16x2(x.tl + RA + y0, x.tl + RA + 128 + y0, re, im);
+                    if constexpr (RAAR) {
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) wp[k] = ld_hint(a.w_proj + (y0 + 8 * hh + k) * M + xcol, pol_keep);
+                        for (int hh = 0; hh < 2; ++hh) {
+                            float2 wp[8];
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const int t = 8 * hh + k;
-                            const int y = y0 + t;
-                            const int o = obj_index(py, px, y, xcol, a.ny, a.nx, WRAP);
-                            const float2 cn = make_float2(re[t] * inv, im[t] * inv);
-                            st_hint(a.c + fo + y * M + xcol, cn, pol_stream);
-                            red_hint(a.accA + o, cmulc(wp[k], cn), pol_keep);
-                            if (a.write_e) red_hint(a.ebuf + fo + y * M + xcol, cn, pol_stream);
+                            for (int k = 0; k < 8; ++k)
+                                wp[k] = ld_hint(a.w_proj + (y0 + 8 * hh + k) * M + xcol, pol_keep);
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const int t = 8 * hh + k;
+                                const int y = y0 + t;
+                                const int o = obj_index(py, px, y, xcol, a.ny, a.nx, WRAP);
+                                const float2 cn = make_float2(re[t] * inv, im[t] * inv);
+                                st_hint(a.c + fo + y * M + xcol, cn, pol_stream);
+                                red_hint(a.accA + o, cmulc(wp[k], cn), pol_keep);
+                                if (a.write_e) red_hint(a.ebuf + fo + y * M + xcol, cn, pol_stream);
+                            }
                         }
-                    }
-                } else {
+                    } else {
 #pragma unroll
-                    for (int t = 0; t < 16; ++t)
-                        st_hint(a.zout + fo + (y0 + t) * M + xcol, make_float2(re[t] * inv, im[t] * inv),
-                                pol_stream);
+                        for (int t = 0; t < 16; ++t)
+                            st_hint(a.zout + fo + (y0 + t) * M + xcol, make_float2(re[t] * inv, im[t] * inv),
+                                    pol_stream);
+                    }
                 }
             }
         }
-        // every thread is past its reads of P before the next frame's load
-        // phase overwrites it (each thread only touches its own lane and
-        // columns, so program order suffices)
+        // each thread only touches its own lane and columns of the region,
+        // so the next frame's load phase may overwrite them in program order
     }
 
-    if (!ok) {
-        // a completion wait gave up: wait (bounded) once more for the MMAs
-        // in flight, flag the failure, release TMEM and leave the sums alone
-        mbar_wait(&bar, x.phase);
-        if (tid == 0) atomicExch(a.err, SHARP_ERR_TIMEOUT);
+    if (!ok) mbar_wait(x.bar, x.phase);   // a wait gave up: wait (bounded) once more for the group's MMAs
+    const bool all_ok = __syncthreads_and(ok);
+    if (!all_ok) {
+        if (tid == 0) atomicExch(a.err, SHARP_ERR_TIMEOUT);   // flag the failure, leave the sums alone
     } else {
         block_sum<G::NT, 5>(acc, red);
         if (tid == 0) {
@@ -497,7 +574,8 @@ static cudaError_t launch_mixed_one(const FrameArgs& a, cudaStream_t s) {
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const int grid = a.K < sms ? a.K : sms;
+    const int need = (a.K + G::NG - 1) / G::NG;
+    const int grid = need < sms ? need : sms;
     kern<<<grid, G::NT, G::SMEM, s>>>(a);
     return cudaGetLastError();
 }

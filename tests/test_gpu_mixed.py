@@ -191,7 +191,10 @@ def test_mixed_nrmse_trajectory_against_oracle(prec):
     # noiseless 6 x 6 raster of 128^2 frames, known probe, 100 iterations:
     # eps_0 (Eq. 14) of the mixed-precision reconstruction tracks the FP64
     # oracle's within 1.02x while the oracle is above the mode's floor
-    # (1e-4 for BF16x3, 3e-3 for FP16), and ends below the floor x 3
+    # (2e-5 for BF16x3, 3e-3 for FP16) and ends below a bound twice the floor
+    # measured on GB300 (BF16x3 ~6e-6, FP16 4.2e-4 .. 5.1e-4: FP16 operand
+    # rounding, which stops the iteration near the paper's 5e-4 target of
+    # Sec. 3.1, while the FP64 oracle reaches 8.7e-9)
     S = _lib()
     m, shape, obj, w, pos, a, psi0, e_ref = _convergence_case()
     n_it = len(e_ref)
@@ -199,7 +202,8 @@ def test_mixed_nrmse_trajectory_against_oracle(prec):
     plan.raar_init(dev(psi0), dev(w))
     ta = dev(a, torch.float32)
     tobj, tw = dev(obj), dev(w)
-    floor = {"bf16x3": 1e-4, "fp16s": 3e-3}[prec]
+    floor = {"bf16x3": 2e-5, "fp16s": 3e-3}[prec]
+    final = {"bf16x3": 2e-5, "fp16s": 1e-3}[prec]
     ratios, e_gpu = {}, None
     for it in range(1, n_it + 1):
         plan.raar_step(ta, metrics=False)
@@ -210,7 +214,7 @@ def test_mixed_nrmse_trajectory_against_oracle(prec):
     for it, (g, r) in ratios.items():
         if r > floor:
             assert g <= 1.02 * r, (it, g, r)
-    assert e_gpu < max(3 * floor, 1.02 * e_ref[-1])
+    assert e_gpu < final
 
 
 def test_mixed_modes_reject_other_frame_sizes_and_batches():
