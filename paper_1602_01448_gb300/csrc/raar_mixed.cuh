@@ -266,10 +266,12 @@ __device__ __forceinline__ float mix_region_max(const MixCtx& x, uint32_t src) {
     return mix_group_max<PREC>(x, mx);
 }
 
-// Wait (bounded) for the group's MMAs; false if the wait gave up.
+// Wait (bounded) for the group's MMAs; false if the wait gave up.  The
+// leader polls the mbarrier; the group's other threads wait at the group
+// barrier and order their later TMEM accesses after it.
 template <int PREC>
 __device__ __forceinline__ bool mix_wait(MixCtx& x) {
-    const bool ok = group_and(mbar_wait(x.bar, x.phase), x.bar_id, MixGeo<PREC>::GT);
+    const bool ok = group_and(x.leader ? mbar_wait(x.bar, x.phase) : true, x.bar_id, MixGeo<PREC>::GT);
     if (!ok) return false;
     x.phase ^= 1u;
     tc_fence_after();
@@ -373,6 +375,24 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     const int xcol = x.r;   // frame column n2 owned by this thread
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     bool ok = true;
+
+    // The frame inputs streamed from HBM (state or input frames, eps_Delta
+    // buffer) of a group's next frame are prefetched into L2 when the group
+    // starts the epilogue of its current frame (a whole frame ahead they were
+    // evicted again before use), so that the load phase's per-thread loads
+    // mostly wait on L2 rather than on HBM.
+    auto prefetch_frame = [&](int f) {
+        if (f >= a.K) return;
+        const size_t o = (size_t)f * MM;
+        if constexpr (RAAR) {
+            bulk_prefetch_l2(a.c + o, (unsigned)(MM * sizeof(float2)));
+            if constexpr (FLAGS & RF_METRIC)
+                if (a.read_e) bulk_prefetch_l2(a.ebuf + o, (unsigned)(MM * sizeof(float2)));
+        } else {
+            bulk_prefetch_l2(a.zin + o, (unsigned)(MM * sizeof(float2)));
+        }
+    };
+    if (x.leader) prefetch_frame(blockIdx.x * G::NG + grp);
 
     for (int i = blockIdx.x * G::NG + grp; i < a.K; i += gridDim.x * G::NG) {
         const size_t fo = (size_t)i * MM;
@@ -502,6 +522,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         if (!ok) break;
 
         // ------------------------------------------------ epilogue from RA
+        if (x.leader) prefetch_frame(i + gridDim.x * G::NG);
         {
             const float inv = 1.f / (g2 * g3);
 #pragma unroll
@@ -512,15 +533,13 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                     float re[16], im[16];
                     tmem_ld16x2(x.tl + RA + y0, x.tl + RA + 128 + y0, re, im);
                     if constexpr (RAAR) {
+                        {
+                            float2 wp[16];
 #pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            float2 wp[8];
+                            for (int k = 0; k < 16; ++k) wp[k] = ld_hint(a.w_proj + (y0 + k) * M + xcol, pol_keep);
 #pragma unroll
-                            for (int k = 0; k < 8; ++k)
-                                wp[k] = ld_hint(a.w_proj + (y0 + 8 * hh + k) * M + xcol, pol_keep);
-#pragma unroll
-                            for (int k = 0; k < 8; ++k) {
-                                const int t = 8 * hh + k;
+                            for (int k = 0; k < 16; ++k) {
+                                const int t = k;
                                 const int y = y0 + t;
                                 const int o = obj_index(py, px, y, xcol, a.ny, a.nx, WRAP);
                                 const float2 cn = make_float2(re[t] * inv, im[t] * inv);
@@ -542,7 +561,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         // so the next frame's load phase may overwrite them in program order
     }
 
-    if (!ok) mbar_wait(x.bar, x.phase);   // a wait gave up: wait (bounded) once more for the group's MMAs
+    if (!ok && x.leader) mbar_wait(x.bar, x.phase);   // a wait gave up: wait (bounded) once more for the group's MMAs
     const bool all_ok = __syncthreads_and(ok);
     if (!all_ok) {
         if (tid == 0) atomicExch(a.err, SHARP_ERR_TIMEOUT);   // flag the failure, leave the sums alone
