@@ -365,8 +365,14 @@ def run_ours(args, rank, world):
     amp_dev = [torch.empty_like(amp), torch.empty_like(amp)]
     psi_snap = [torch.empty_like(plan.psi), torch.empty_like(plan.psi)]
     psi_pin = [torch.empty(plan.psi.shape, dtype=plan.psi.dtype, pin_memory=True) for _ in range(2)]
-    up_s, down_s = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-    uploaded = [torch.cuda.Event(), torch.cuda.Event()]
+    # the upload of a step is split into contiguous slices, one copy stream
+    # each, so that several copy engines share the host-to-device transfer
+    n_up = max(1, args.copy_streams)
+    up_s = [torch.cuda.Stream(device=dev) for _ in range(n_up)]
+    down_s = torch.cuda.Stream(device=dev)
+    flat_pin = amp_pin.view(-1)
+    bounds = [(len(flat_pin) * j) // n_up for j in range(n_up + 1)]
+    uploaded = [[torch.cuda.Event() for _ in range(n_up)] for _ in range(2)]
     consumed = [torch.cuda.Event(), torch.cuda.Event()]
     snapped = [torch.cuda.Event(), torch.cuda.Event()]
     read = [torch.cuda.Event(), torch.cuda.Event()]
@@ -377,19 +383,22 @@ def run_ours(args, rank, world):
 
     def upload(k):
         b = k % 2
-        up_s.wait_event(f0)
-        if k >= 2:
-            up_s.wait_event(consumed[b])          # step k-2 is done with this buffer
-        with torch.cuda.stream(up_s):
-            amp_dev[b].copy_(amp_pin, non_blocking=True)
-        uploaded[b].record(up_s)
+        dst = amp_dev[b].view(-1)
+        for j, st in enumerate(up_s):
+            st.wait_event(f0)
+            if k >= 2:
+                st.wait_event(consumed[b])        # step k-2 is done with this buffer
+            with torch.cuda.stream(st):
+                dst[bounds[j]:bounds[j + 1]].copy_(flat_pin[bounds[j]:bounds[j + 1]], non_blocking=True)
+            uploaded[b][j].record(st)
 
     upload(0)
     for k in range(e2e_steps):
         b = k % 2
         if k + 1 < e2e_steps:
             upload(k + 1)
-        stream.wait_event(uploaded[b])
+        for ev in uploaded[b]:
+            stream.wait_event(ev)
         if k >= 2:
             stream.wait_event(read[b])           # snapshot buffer b was read back
         plan.raar_step(amp_dev[b])
@@ -441,7 +450,8 @@ def run_ours(args, rank, world):
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "cpu_baseline": cpu,
         "e2e": {"value": world * K / (e2e_ms / 1000.0), "unit": UNIT,
-                "h2d_bytes_per_step": int(amp.numel() * 4), "d2h_bytes_per_step": int(plan.psi.numel() * 8)},
+                "h2d_bytes_per_step": int(amp.numel() * 4), "d2h_bytes_per_step": int(plan.psi.numel() * 8),
+                "ms_per_step": e2e_ms, "copy_streams": n_up},
         "gpu_launches": launches,
         "clocks": clocks,
         "last_metrics": {"eps_a": metrics[0], "eps_q": metrics[1]},
@@ -578,6 +588,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the tensor-core precision modes (128^2 frames)")
+    ap.add_argument("--copy-streams", type=int, default=1,
+                    help="copy streams sharing each step's host-to-device upload in the e2e measurement")
     ap.add_argument("--workload", default="fermat", choices=["fermat", "raster256", "batch", "batch-small"])
     ap.add_argument("--frames", type=int, default=None,
                     help="frames of the scan (default: the workload's; fewer for small ncu captures; "

@@ -230,3 +230,34 @@ def test_mixed_modes_reject_other_frame_sizes_and_batches():
     plan.raar_init(dev(obj), dev(w))
     with pytest.raises(S.SharpError):
         S.Batch([plan], [dev(np.ones((len(pos), 128, 128)), torch.float32)])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("K", [1, 3, 305])
+def test_mixed_projection_ragged_frame_counts(prec, K):
+    # a single frame, an odd count (a frame group without work) and one frame
+    # more than two per SM (one group takes a second frame)
+    S = _lib()
+    rng = np.random.default_rng(K)
+    m = 128
+    pos = np.zeros((K, 2), np.int32)
+    plan = S.Plan(pos, m, (m, m), precision=prec)
+    z = synth.random_frames(K, m, 100 + K)
+    a = np.abs(synth.random_amplitudes(K, m, 200 + K) * (1 + 0.1 * rng.standard_normal((K, m, m))))
+    out, r = plan.fourier_project(dev(z), dev(a, torch.float32))
+    ref = O.data_project(z, a.astype(np.float32).astype(np.float64))
+    got = host(out)
+    assert rel_l2(got, ref) < TOL[prec]
+    assert rel_l2(got[-1], ref[-1]) < TOL[prec]
+    rr = O.norm(ref - z) ** 2
+    assert abs(r.item() - rr) < 3 * TOL[prec] * rr
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_mixed_full_size_fermat_step_on_sampled_outputs(prec):
+    # the benchmark's workload and launch configuration: 2500 frames of 128^2
+    # on a Fermat spiral over a 1024^2 object; sampled frames and an object
+    # patch against the oracle (the step's input state comes from a first
+    # mixed-precision step, so the bound is that of one projection)
+    from tests.test_gpu_raar import _sampled_step_parity
+    _sampled_step_parity(synth.scan_fermat(), (500, 520, 6), precision=prec, tol=TOL[prec])
