@@ -32,24 +32,28 @@
 // D_i = A_r B_i +- A_i B_r (the sign of the A_i terms through the
 // instruction's negate-A bit: forward F, inverse F*).
 //
-// Frame groups.  A block of 512 threads (16 warps, one block per SM) runs NG
-// frame groups, each an independent pipeline over its own frames with its own
-// TMEM columns, B buffer, mbarrier and named barrier; the DFT matrix is
-// shared.  Thread t of a group owns TMEM lane r = 32 (w % 4) + lane and, in
-// each of the two K-chunks j of 64 columns, the CW columns
-// 64 j + CW (w_g / 4) + [0, CW); in frame coordinates that is one column
-// index n2 = r (coalesced global accesses across a warp) and 2 CW row
-// indices.
-//  - FP16S: two groups of 256 threads (CW = 32).  A stage converts all of its
-//    input (both K-chunks, 64 KB of B) before it issues any MMA, so the
-//    result can overwrite the input in place: a frame needs 256 TMEM columns
-//    (real part in 0-127, imaginary in 128-255) and the two groups fill all
-//    512.  While one group waits on memory (gathers, amplitudes, scatter) the
-//    other group's contractions run.
-//  - BF16X3: one group of 512 threads (CW = 16).  Its operands are twice as
-//    large (hi and lo parts), so B holds one K-chunk at a time and a stage
-//    alternates between two 256-column regions P and Q
-//    (z in P -> D1 in Q -> D2 in P -> D3 in Q -> D4 in P).
+// Thread layout.  A block of 512 threads (16 warps, one block per SM) walks
+// its frames one at a time.  Thread t owns TMEM lane r = 32 (w % 4) + lane
+// and, in each of the two K-chunks j of 64 columns, the CW = 16 columns
+// 64 j + 16 (w / 4) + [0, 16); in frame coordinates that is one column index
+// n2 = r (coalesced global accesses across a warp) and 32 row indices.  The
+// code keeps a frame-group index (NG groups of NT / NG threads with their own
+// B buffer, mbarrier and named barrier; NG = 1 here): two FP16 groups per
+// block, each transforming in place in 256 TMEM columns, were measured no
+// faster than one, because the memory phases of the two groups share the
+// SM's outstanding requests.
+// Stages alternate between two 256-column TMEM regions P and Q (z in P ->
+// D1 in Q -> D2 in P -> D3 in Q -> D4 in P; real part in columns 0-127 of a
+// region, imaginary part in 128-255).
+//  - FP16S: B holds both K-chunks of a stage (64 KB), so the second chunk is
+//    converted while the MMAs of the first run.  The frame's input (state,
+//    or the frames of P_a) is copied into shared memory by two bulk copies
+//    (rows 0-63 into a staging buffer, rows 64-127 into the B buffer, idle
+//    from the last MMA of one frame to the first conversion of the next),
+//    issued when the previous frame's epilogue starts.
+//  - BF16X3: its operands are twice as large (hi and lo parts), so B holds
+//    one K-chunk at a time; the input frame is read by the threads after an
+//    L2 prefetch issued at the previous epilogue.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -65,7 +69,7 @@ struct MixGeo {
     static constexpr int M = 128;
     static constexpr int NT = 512;
     static constexpr bool F16 = PREC == SHARP_PREC_FP16S;
-    static constexpr int NG = F16 ? 2 : 1;              // frame groups per block
+    static constexpr int NG = 1;                        // frame groups per block
     static constexpr int GT = NT / NG;                  // threads per group
     static constexpr int GW = GT / 32;                  // warps per group
     static constexpr int CW = 64 / (GW / 4);            // columns per thread per K-chunk
@@ -76,7 +80,13 @@ struct MixGeo {
     static constexpr int A_BYTES = NPART * A_PART;
     static constexpr int B_SLOT = NPART * B_PART;
     static constexpr int B_GROUP = NBUF * B_SLOT;
-    static constexpr int SMEM = A_BYTES + NG * B_GROUP + 128;
+    // FP16S stages each frame's input (state or frames, complex64) in shared
+    // memory by TMA: rows 0-63 in CBUF, rows 64-127 in the B buffer, which is
+    // idle between the last contraction of one frame and the first of the next
+    static constexpr bool STAGE = F16;
+    static constexpr int CBUF = STAGE ? 64 * M * 8 : 0;
+    static_assert(!STAGE || B_GROUP == 64 * M * 8, "the B buffer holds the second half of a staged frame");
+    static constexpr int SMEM = A_BYTES + NG * B_GROUP + CBUF + 128;
     static constexpr uint32_t LBO = 16 * 128;           // K-adjacent core matrices (16 row groups of 128 B)
     static constexpr uint32_t SBO = 128;                // row-group-adjacent core matrices
     static_assert(SMEM <= 232448, "shared memory of one block");
@@ -279,22 +289,24 @@ __device__ __forceinline__ bool mix_wait(MixCtx& x) {
 }
 
 // One contraction stage: region dst = F(or F*) . (g * region src)^T in the
-// stage layout above (dst == src for FP16S: the whole input is in shared
-// memory before the first MMA).  False if an MMA completion wait gave up.
+// stage layout above.  False if an MMA completion wait gave up.
 template <int PREC>
 __device__ __forceinline__ bool mix_stage(MixCtx& x, uint32_t src, uint32_t dst, bool inverse, float g) {
     using G = MixGeo<PREC>;
     if constexpr (G::NBUF == 2) {
+        // both K-chunks in their own buffers: chunk 1 is converted while the
+        // MMAs of chunk 0 run (src != dst)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) mix_convert<PREC>(x, src, j, x.sB + j * G::B_SLOT, g);
-        fence_proxy_async_smem();   // generic-proxy writes -> tensor-core (async proxy) reads
-        tc_fence_before();
-        group_bar(x.bar_id, G::GT);
-        if (x.leader) {
-            tc_fence_after();
-            mix_issue<PREC>(x.sA, x.sB, x.tbase + dst, 0, inverse);
-            mix_issue<PREC>(x.sA, x.sB + G::B_SLOT, x.tbase + dst, 1, inverse);
-            mma_commit(x.bar);
+        for (int j = 0; j < 2; ++j) {
+            mix_convert<PREC>(x, src, j, x.sB + j * G::B_SLOT, g);
+            fence_proxy_async_smem();   // generic-proxy writes -> tensor-core (async proxy) reads
+            tc_fence_before();
+            group_bar(x.bar_id, G::GT);
+            if (x.leader) {
+                tc_fence_after();
+                mix_issue<PREC>(x.sA, x.sB + j * G::B_SLOT, x.tbase + dst, j, inverse);
+                if (j == 1) mma_commit(x.bar);
+            }
         }
         return mix_wait<PREC>(x);
     } else {
@@ -325,6 +337,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     extern __shared__ __align__(128) unsigned char mix_smem[];
     __shared__ FrameArgs a;
     __shared__ __align__(8) uint64_t bars[G::NG];
+    __shared__ __align__(8) uint64_t cbar;   // staged frame input arrived
     __shared__ uint32_t s_tmem;
     __shared__ float s_max[16];
     __shared__ float red[32 * 5];
@@ -351,6 +364,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     if (tid == 0) {
         a = ap;
         for (int k = 0; k < G::NG; ++k) mbar_init(&bars[k], 1);
+        mbar_init(&cbar, 1);
         mbar_fence_init();
     }
     if (warp == 0) {
@@ -363,10 +377,12 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     tc_fence_after();
     x.tbase = s_tmem;
     x.tl = x.tbase + ((uint32_t)(32 * (warp & 3)) << 16);
-    // TMEM regions: FP16S works in place in the group's 256 columns; BF16X3
-    // alternates between P = 0 and Q = 256
-    const uint32_t RA = G::F16 ? 256u * grp : 0u;
-    const uint32_t RB = G::F16 ? RA : 256u;
+    // TMEM regions: stages alternate between P = 0 and Q = 256
+    const uint32_t RA = 0u;
+    const uint32_t RB = 256u;
+    unsigned char* const sbase = mix_smem + (x.sA - smem_addr(mix_smem));
+    const float2* const stage_lo = reinterpret_cast<const float2*>(sbase + G::A_BYTES + G::NG * G::B_GROUP);
+    const float2* const stage_hi = reinterpret_cast<const float2*>(sbase + G::A_BYTES);
 
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
@@ -381,8 +397,25 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     // starts the epilogue of its current frame (a whole frame ahead they were
     // evicted again before use), so that the load phase's per-thread loads
     // mostly wait on L2 rather than on HBM.
+    // FP16S instead copies the whole input frame into shared memory (two bulk
+    // copies of 64 rows) at the same point, and the load phase reads it there.
+    unsigned cpar = 0;
+    bool st_pending = false;                  // uniform across the block
+    auto stage_frame = [&](int f) {           // leader only
+        const float2* src = (RAAR ? a.c : a.zin) + (size_t)f * MM;
+        mbar_expect_tx(&cbar, (unsigned)(MM * sizeof(float2)));
+        bulk_g2s_hint(const_cast<float2*>(stage_lo), src, (unsigned)(64 * M * sizeof(float2)), &cbar, pol_stream);
+        bulk_g2s_hint(const_cast<float2*>(stage_hi), src + 64 * M, (unsigned)(64 * M * sizeof(float2)), &cbar,
+                      pol_stream);
+    };
     auto prefetch_frame = [&](int f) {
         if (f >= a.K) return;
+        if constexpr (G::STAGE) {
+            if constexpr (RAAR && (FLAGS & RF_METRIC))
+                if (a.read_e) bulk_prefetch_l2(a.ebuf + (size_t)f * MM, (unsigned)(MM * sizeof(float2)));
+            stage_frame(f);
+            return;
+        }
         const size_t o = (size_t)f * MM;
         if constexpr (RAAR) {
             bulk_prefetch_l2(a.c + o, (unsigned)(MM * sizeof(float2)));
@@ -393,6 +426,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         }
     };
     if (x.leader) prefetch_frame(blockIdx.x * G::NG + grp);
+    if constexpr (G::STAGE) st_pending = blockIdx.x * G::NG + grp < a.K;
 
     for (int i = blockIdx.x * G::NG + grp; i < a.K; i += gridDim.x * G::NG) {
         const size_t fo = (size_t)i * MM;
@@ -401,6 +435,12 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         const int px = RAAR ? a.pos[2 * i + 1] : 0;
 
         // ------------------------------------------------ load: z into RA
+        if constexpr (G::STAGE) {
+            ok = group_and(mbar_wait(&cbar, cpar), x.bar_id, G::GT);
+            if (!ok) break;
+            cpar ^= 1u;
+            st_pending = false;
+        }
         float mx = 0.f;
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -414,7 +454,8 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                     for (int k = 0; k < 8; ++k) {
                         const int y = y0 + k;
                         const int o = obj_index(py, px, y, xcol, a.ny, a.nx, WRAP);
-                        cv[k] = ld_hint(a.c + fo + y * M + xcol, pol_stream);
+                        if constexpr (G::STAGE) cv[k] = (j == 0 ? stage_lo : stage_hi)[(y - 64 * j) * M + xcol];
+                        else cv[k] = ld_hint(a.c + fo + y * M + xcol, pol_stream);
                         wf[k] = ld_hint(a.w_form + y * M + xcol, pol_keep);
                         yv[k] = ld_hint(a.psiy + o, pol_keep);
                         if constexpr (FLAGS & RF_FORM_B) wp[k] = ld_hint(a.w_proj + y * M + xcol, pol_keep);
@@ -445,7 +486,10 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                 } else {
                     float2 zv[8];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) zv[k] = ld_hint(a.zin + fo + (y0 + k) * M + xcol, pol_stream);
+                    for (int k = 0; k < 8; ++k) {
+                        if constexpr (G::STAGE) zv[k] = (j == 0 ? stage_lo : stage_hi)[(y0 + k - 64 * j) * M + xcol];
+                        else zv[k] = ld_hint(a.zin + fo + (y0 + k) * M + xcol, pol_stream);
+                    }
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         zr[k] = zv[k].x;
@@ -522,7 +566,10 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         if (!ok) break;
 
         // ------------------------------------------------ epilogue from RA
+        // (the staging buffers are free: the load phase is done and the last
+        // contraction's MMAs, which read the B buffer, have completed)
         if (x.leader) prefetch_frame(i + gridDim.x * G::NG);
+        if constexpr (G::STAGE) st_pending = i + gridDim.x * G::NG < a.K;
         {
             const float inv = 1.f / (g2 * g3);
 #pragma unroll
@@ -562,6 +609,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     }
 
     if (!ok && x.leader) mbar_wait(x.bar, x.phase);   // a wait gave up: wait (bounded) once more for the group's MMAs
+    if (st_pending && x.leader) mbar_wait(&cbar, cpar);   // and for a staging copy still in flight
     const bool all_ok = __syncthreads_and(ok);
     if (!all_ok) {
         if (tid == 0) atomicExch(a.err, SHARP_ERR_TIMEOUT);   // flag the failure, leave the sums alone
