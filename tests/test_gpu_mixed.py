@@ -264,3 +264,40 @@ def test_mixed_full_size_fermat_step_on_sampled_outputs(prec):
     # (BF16x3 measured 5.7e-5 on one of the sampled frames)
     from tests.test_gpu_raar import _sampled_step_parity
     _sampled_step_parity(synth.scan_fermat(), (500, 520, 6), precision=prec, tol=2 * TOL[prec])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("beta", [1.0, 0.55])
+def test_mixed_raar_beta_extremes_match_oracle(prec, beta):
+    # beta = 1 is Douglas-Rachford (2 P_Q P_a - P_Q - P_a + I); beta near 1/2
+    # makes 1/(1-2b) in the image pass large (Sec. 2.2 update)
+    S = _lib()
+    obj, w, pos, shape, a = _noisy_scan(3, 24, 21, seed=13, photons=1e6)
+    psi0 = synth.random_object(shape, np.random.default_rng(14), phase_sigma=1.0)
+    ref = O.raar_reconstruct(a, pos, shape, w, psi0, 3, beta=beta)
+    plan = S.Plan(pos, 128, shape, beta=beta, residual_every=1, precision=prec)
+    plan.raar_init(dev(psi0), dev(w))
+    ta = dev(a, torch.float32)
+    for step_i in range(3):
+        met = host(plan.raar_step(ta)).real
+        _check_metrics(met, ref["history"][step_i], MET[prec])
+    D = O.illumination(w, pos, shape)
+    vis = D > 1e-3 * D.max()
+    amp_1_2b = 1 + 4 * (beta < 0.6)
+    assert rel_l2(host(plan.psi), ref["psi"], vis) < 6 * TOL[prec] * amp_1_2b
+
+
+def test_mixed_projection_rejects_misaligned_frames():
+    # the tensor-core P_a stages its input with 16-byte bulk copies
+    S = _lib()
+    pos, obj, w, shape = _case()
+    K, m = len(pos), 128
+    plan = S.Plan(pos, m, shape, precision="fp16s")
+    buf = torch.zeros(K * m * m + 1, dtype=torch.complex64, device="cuda")
+    z = buf[1:].view(K, m, m)
+    assert z.data_ptr() % 16 == 8
+    a = dev(synth.random_amplitudes(K, m, 3), torch.float32)
+    out = torch.empty((K, m, m), dtype=torch.complex64, device="cuda")
+    with pytest.raises(S.SharpError) as ei:
+        S.sharp_fourier_project(plan.handle, z, a, out)
+    assert "INVALID_ARG" in str(ei.value)

@@ -264,3 +264,34 @@ def test_full_size_large_raster_step_on_sampled_outputs():
 def test_full_size_wrapped_raster_step_on_sampled_outputs():
     # 1600 frames of 128^2 on a 40 x 40 raster over a periodic 512^2 object
     _sampled_step_parity(synth.scan_wrapped_raster(), (250, 260, 6))
+
+
+def test_large_frames_nrmse_trajectory_against_oracle():
+    # 256^2 frames (the 10^4-frame raster's frame size, step 24 +-1 px and
+    # probe) on a 10 x 10 raster, noiseless, known probe, flat start, 16
+    # steps: eps_0 (Eq. 14) of the GPU object stays within 1.02x of the FP64
+    # oracle's at every 4th step
+    S = _lib()
+    rng = np.random.default_rng(23)
+    m = 256
+    shape = (9 * 24 + m + 64,) * 2
+    obj = synth.random_object(shape, rng)
+    w = synth.gaussian_probe(m, 40.0, rng)
+    pos = synth.raster_positions(10, 10, 24, m, shape, rng, jitter=1)
+    a = O.forward_amplitudes(obj, w, pos).astype(np.float32).astype(np.float64)
+    psi0 = np.ones(shape, complex)
+    n_it = 16
+    ref = O.raar_reconstruct(a, pos, shape, w, psi0, n_it, psi_true=obj, record_metrics=False)
+    e_ref = [h["eps_0"] for h in ref["history"]]
+    plan = S.Plan(pos, m, shape, residual_every=0)
+    plan.raar_init(dev(psi0), dev(w))
+    ta = dev(a, torch.float32)
+    tobj, tw = dev(obj), dev(w)
+    out = {}
+    for it in range(1, n_it + 1):
+        plan.raar_step(ta, metrics=False)
+        if it % 4 == 0:
+            out[it] = (plan.solution_error(plan.psi, tobj, tw)[0].item(), e_ref[it - 1])
+    print("256^2 eps_0 (GPU, oracle):", {k: (f"{g:.4e}", f"{r:.4e}") for k, (g, r) in out.items()})
+    for it, (g, r) in out.items():
+        assert abs(g / r - 1) <= 0.02, (it, g, r)
