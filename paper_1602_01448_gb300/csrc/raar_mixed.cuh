@@ -36,12 +36,10 @@
 // its frames one at a time.  Thread t owns TMEM lane r = 32 (w % 4) + lane
 // and, in each of the two K-chunks j of 64 columns, the CW = 16 columns
 // 64 j + 16 (w / 4) + [0, 16); in frame coordinates that is one column index
-// n2 = r (coalesced global accesses across a warp) and 32 row indices.  The
-// code keeps a frame-group index (NG groups of NT / NG threads with their own
-// B buffer, mbarrier and named barrier; NG = 1 here): two FP16 groups per
-// block, each transforming in place in 256 TMEM columns, were measured no
-// faster than one, because the memory phases of the two groups share the
-// SM's outstanding requests.
+// n2 = r (coalesced global accesses across a warp) and 32 row indices.  (Two
+// independent 256-thread frame groups per block, each transforming in place
+// in 256 TMEM columns, were measured no faster than one block-wide pipeline:
+// the memory phases of the two groups share the SM's outstanding requests.)
 // Stages alternate between two 256-column TMEM regions P and Q (z in P ->
 // D1 in Q -> D2 in P -> D3 in Q -> D4 in P; real part in columns 0-127 of a
 // region, imaginary part in 128-255).
@@ -69,24 +67,22 @@ struct MixGeo {
     static constexpr int M = 128;
     static constexpr int NT = 512;
     static constexpr bool F16 = PREC == SHARP_PREC_FP16S;
-    static constexpr int NG = 1;                        // frame groups per block
-    static constexpr int GT = NT / NG;                  // threads per group
-    static constexpr int GW = GT / 32;                  // warps per group
-    static constexpr int CW = 64 / (GW / 4);            // columns per thread per K-chunk
+    static constexpr int NW = NT / 32;                  // warps
+    static constexpr int CW = 64 / (NW / 4);            // columns per thread per K-chunk (16)
     static constexpr int NPART = F16 ? 2 : 4;           // operand parts: {re, im} or {re_hi, re_lo, im_hi, im_lo}
     static constexpr int NBUF = F16 ? 2 : 1;            // K-chunks of 64 held in B at once
     static constexpr int A_PART = M * M * 2;            // 32 KB: one 128 x 128 16-bit matrix
     static constexpr int B_PART = M * 64 * 2;           // 16 KB: 128 rows x one K-chunk of 64
     static constexpr int A_BYTES = NPART * A_PART;
     static constexpr int B_SLOT = NPART * B_PART;
-    static constexpr int B_GROUP = NBUF * B_SLOT;
+    static constexpr int B_BYTES = NBUF * B_SLOT;
     // FP16S stages each frame's input (state or frames, complex64) in shared
     // memory by TMA: rows 0-63 in CBUF, rows 64-127 in the B buffer, which is
     // idle between the last contraction of one frame and the first of the next
     static constexpr bool STAGE = F16;
     static constexpr int CBUF = STAGE ? 64 * M * 8 : 0;
-    static_assert(!STAGE || B_GROUP == 64 * M * 8, "the B buffer holds the second half of a staged frame");
-    static constexpr int SMEM = A_BYTES + NG * B_GROUP + CBUF + 128;
+    static_assert(!STAGE || B_BYTES == 64 * M * 8, "the B buffer holds the second half of a staged frame");
+    static constexpr int SMEM = A_BYTES + B_BYTES + CBUF + 128;
     static constexpr uint32_t LBO = 16 * 128;           // K-adjacent core matrices (16 row groups of 128 B)
     static constexpr uint32_t SBO = 128;                // row-group-adjacent core matrices
     static_assert(SMEM <= 232448, "shared memory of one block");
@@ -94,23 +90,6 @@ struct MixGeo {
     static_assert(CW % 16 == 0, "TMEM accesses of 16 columns");
 };
 
-// ------------------------------------------------------------ group sync
-__device__ __forceinline__ void group_bar(int id, int count) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-// Barrier of the group that also ANDs a predicate over its threads.
-__device__ __forceinline__ bool group_and(bool v, int id, int count) {
-    int r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.b32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, %2, %3, p;\n\t"
-        "selp.s32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((int)v), "r"(id), "r"(count)
-        : "memory");
-    return r != 0;
-}
 
 // Power of two 2^e with mx 2^e in [2^14, 2^15) (1 for 0, Inf or NaN).
 __device__ __forceinline__ float mix_pow2_scale(float mx) {
@@ -143,32 +122,31 @@ __device__ __forceinline__ void split_b2(float x, float y, uint32_t& hi, uint32_
     lo = pack_b2(__float2bfloat16_rn(x - __bfloat162float(hx)), __float2bfloat16_rn(y - __bfloat162float(hy)));
 }
 
-// Per-thread state of a frame group.
+// Per-thread state of the pipeline.
 struct MixCtx {
     uint32_t sA;           // shared address of the DFT matrix parts
-    uint32_t sB;           // this group's B buffer
+    uint32_t sB;           // shared address of the B buffer
     uint32_t tbase;        // TMEM base (lane 0, column 0)
     uint32_t tl;           // TMEM address of this warp's lane quarter
     int r, h;              // TMEM lane (frame index owned) and column group
-    int bar_id;            // named barrier of the group
-    bool leader;           // issues the group's MMAs
-    uint64_t* bar;         // MMA completion of the group
-    float* s_max;          // GW floats
+    bool leader;           // issues the MMAs and the bulk copies (thread 0)
+    uint64_t* bar;         // MMA completion
+    float* s_max;          // one float per warp
     unsigned phase;
 };
 
-// Largest value over the group (all its threads receive it).
+// Largest value over the block (all threads receive it).
 template <int PREC>
-__device__ __forceinline__ float mix_group_max(const MixCtx& x, float v) {
+__device__ __forceinline__ float mix_block_max(const MixCtx& x, float v) {
     using G = MixGeo<PREC>;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    group_bar(x.bar_id, G::GT);
-    if ((threadIdx.x & 31) == 0) x.s_max[(threadIdx.x % G::GT) >> 5] = v;
-    group_bar(x.bar_id, G::GT);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) x.s_max[threadIdx.x >> 5] = v;
+    __syncthreads();
     float m = x.s_max[0];
 #pragma unroll
-    for (int k = 1; k < G::GW; ++k) m = fmaxf(m, x.s_max[k]);
+    for (int k = 1; k < G::NW; ++k) m = fmaxf(m, x.s_max[k]);
     return m;
 }
 
@@ -207,7 +185,7 @@ __device__ __forceinline__ void mix_put16(uint32_t sb, int r, int kg, const floa
     }
 }
 
-// MMAs of K-chunk j of one stage (the group leader): D (columns d, d + 128)
+// MMAs of K-chunk j of one stage (thread 0): D (columns d, d + 128)
 // (+)= F(or F*)[:, 64 j .. 64 j + 63] . B(chunk in sb)^T.
 template <int PREC>
 __device__ __forceinline__ void mix_issue(uint32_t sA, uint32_t sb, uint32_t d, int j, bool inverse) {
@@ -257,7 +235,7 @@ __device__ __forceinline__ void mix_convert(const MixCtx& x, uint32_t src, int j
     }
 }
 
-// Largest component of region `src` over the group.
+// Largest component of region `src` over the block.
 template <int PREC>
 __device__ __forceinline__ float mix_region_max(const MixCtx& x, uint32_t src) {
     using G = MixGeo<PREC>;
@@ -273,15 +251,15 @@ __device__ __forceinline__ float mix_region_max(const MixCtx& x, uint32_t src) {
             for (int t = 0; t < 16; ++t) mx = fmaxf(mx, fmaxf(fabsf(re[t]), fabsf(im[t])));
         }
     }
-    return mix_group_max<PREC>(x, mx);
+    return mix_block_max<PREC>(x, mx);
 }
 
-// Wait (bounded) for the group's MMAs; false if the wait gave up.  The
-// leader polls the mbarrier; the group's other threads wait at the group
-// barrier and order their later TMEM accesses after it.
+// Wait (bounded) for the issued MMAs; false if the wait gave up.  The leader
+// polls the mbarrier; the other threads wait at the block barrier and order
+// their later TMEM accesses after it.
 template <int PREC>
 __device__ __forceinline__ bool mix_wait(MixCtx& x) {
-    const bool ok = group_and(x.leader ? mbar_wait(x.bar, x.phase) : true, x.bar_id, MixGeo<PREC>::GT);
+    const bool ok = __syncthreads_and(x.leader ? mbar_wait(x.bar, x.phase) : true);
     if (!ok) return false;
     x.phase ^= 1u;
     tc_fence_after();
@@ -301,7 +279,7 @@ __device__ __forceinline__ bool mix_stage(MixCtx& x, uint32_t src, uint32_t dst,
             mix_convert<PREC>(x, src, j, x.sB + j * G::B_SLOT, g);
             fence_proxy_async_smem();   // generic-proxy writes -> tensor-core (async proxy) reads
             tc_fence_before();
-            group_bar(x.bar_id, G::GT);
+            __syncthreads();
             if (x.leader) {
                 tc_fence_after();
                 mix_issue<PREC>(x.sA, x.sB + j * G::B_SLOT, x.tbase + dst, j, inverse);
@@ -315,7 +293,7 @@ __device__ __forceinline__ bool mix_stage(MixCtx& x, uint32_t src, uint32_t dst,
             mix_convert<PREC>(x, src, j, x.sB, g);
             fence_proxy_async_smem();
             tc_fence_before();
-            group_bar(x.bar_id, G::GT);
+            __syncthreads();
             if (x.leader) {
                 tc_fence_after();
                 mix_issue<PREC>(x.sA, x.sB, x.tbase + dst, j, inverse);
@@ -336,24 +314,21 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     constexpr bool RAAR = MODE == MODE_RAAR;
     extern __shared__ __align__(128) unsigned char mix_smem[];
     __shared__ FrameArgs a;
-    __shared__ __align__(8) uint64_t bars[G::NG];
+    __shared__ __align__(8) uint64_t bar;    // MMAs completed
     __shared__ __align__(8) uint64_t cbar;   // staged frame input arrived
     __shared__ uint32_t s_tmem;
     __shared__ float s_max[16];
     __shared__ float red[32 * 5];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int grp = warp / G::GW;          // frame group
-    const int wg = warp % G::GW;           // warp within the group
 
     MixCtx x;
     x.sA = (smem_addr(mix_smem) + 127u) & ~127u;
-    x.sB = x.sA + G::A_BYTES + grp * G::B_GROUP;
+    x.sB = x.sA + G::A_BYTES;
     x.r = 32 * (warp & 3) + lane;
-    x.h = wg >> 2;
-    x.bar_id = 1 + grp;
-    x.leader = (tid % G::GT) == 0;
-    x.bar = &bars[grp];
-    x.s_max = s_max + grp * G::GW;
+    x.h = warp >> 2;
+    x.leader = tid == 0;
+    x.bar = &bar;
+    x.s_max = s_max;
     x.phase = 0;
 
     {   // DFT matrix parts, already in the operand layout, into shared memory
@@ -363,7 +338,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     }
     if (tid == 0) {
         a = ap;
-        for (int k = 0; k < G::NG; ++k) mbar_init(&bars[k], 1);
+        mbar_init(&bar, 1);
         mbar_init(&cbar, 1);
         mbar_fence_init();
     }
@@ -381,7 +356,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     const uint32_t RA = 0u;
     const uint32_t RB = 256u;
     unsigned char* const sbase = mix_smem + (x.sA - smem_addr(mix_smem));
-    const float2* const stage_lo = reinterpret_cast<const float2*>(sbase + G::A_BYTES + G::NG * G::B_GROUP);
+    const float2* const stage_lo = reinterpret_cast<const float2*>(sbase + G::A_BYTES + G::B_BYTES);
     const float2* const stage_hi = reinterpret_cast<const float2*>(sbase + G::A_BYTES);
 
     const uint64_t pol_stream = policy_evict_first();
@@ -393,7 +368,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     bool ok = true;
 
     // The frame inputs streamed from HBM (state or input frames, eps_Delta
-    // buffer) of a group's next frame are prefetched into L2 when the group
+    // buffer) of the block's next frame are prefetched into L2 when the block
     // starts the epilogue of its current frame (a whole frame ahead they were
     // evicted again before use), so that the load phase's per-thread loads
     // mostly wait on L2 rather than on HBM.
@@ -425,10 +400,10 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
             bulk_prefetch_l2(a.zin + o, (unsigned)(MM * sizeof(float2)));
         }
     };
-    if (x.leader) prefetch_frame(blockIdx.x * G::NG + grp);
-    if constexpr (G::STAGE) st_pending = blockIdx.x * G::NG + grp < a.K;
+    if (x.leader) prefetch_frame(blockIdx.x);
+    if constexpr (G::STAGE) st_pending = (int)blockIdx.x < a.K;
 
-    for (int i = blockIdx.x * G::NG + grp; i < a.K; i += gridDim.x * G::NG) {
+    for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
         const size_t fo = (size_t)i * MM;
         if (x.leader) bulk_prefetch_l2(a.amp + fo, (unsigned)(MM * sizeof(float)));
         const int py = RAAR ? a.pos[2 * i] : 0;
@@ -436,7 +411,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
 
         // ------------------------------------------------ load: z into RA
         if constexpr (G::STAGE) {
-            ok = group_and(mbar_wait(&cbar, cpar), x.bar_id, G::GT);
+            ok = __syncthreads_and(mbar_wait(&cbar, cpar));
             if (!ok) break;
             cpar ^= 1u;
             st_pending = false;
@@ -503,7 +478,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         }
         tmem_wait_st();
         float g0 = 1.f, g1 = 1.f, g2 = 1.f, g3 = 1.f;
-        if constexpr (G::F16) g0 = mix_pow2_scale(mix_group_max<PREC>(x, mx));
+        if constexpr (G::F16) g0 = mix_pow2_scale(mix_block_max<PREC>(x, mx));
 
         // ------------------------------------------------ forward transform
         ok = mix_stage<PREC>(x, RA, RB, false, g0);
@@ -555,7 +530,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                 }
             }
             tmem_wait_st();
-            if constexpr (G::F16) g2 = mix_pow2_scale(mix_group_max<PREC>(x, um));
+            if constexpr (G::F16) g2 = mix_pow2_scale(mix_block_max<PREC>(x, um));
         }
 
         // ------------------------------------------------ inverse transform
@@ -568,8 +543,8 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         // ------------------------------------------------ epilogue from RA
         // (the staging buffers are free: the load phase is done and the last
         // contraction's MMAs, which read the B buffer, have completed)
-        if (x.leader) prefetch_frame(i + gridDim.x * G::NG);
-        if constexpr (G::STAGE) st_pending = i + gridDim.x * G::NG < a.K;
+        if (x.leader) prefetch_frame(i + gridDim.x);
+        if constexpr (G::STAGE) st_pending = i + (int)gridDim.x < a.K;
         {
             const float inv = 1.f / (g2 * g3);
 #pragma unroll
@@ -608,7 +583,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         // so the next frame's load phase may overwrite them in program order
     }
 
-    if (!ok && x.leader) mbar_wait(x.bar, x.phase);   // a wait gave up: wait (bounded) once more for the group's MMAs
+    if (!ok && x.leader) mbar_wait(x.bar, x.phase);   // a wait gave up: wait (bounded) once more for the MMAs
     if (st_pending && x.leader) mbar_wait(&cbar, cpar);   // and for a staging copy still in flight
     const bool all_ok = __syncthreads_and(ok);
     if (!all_ok) {
@@ -641,8 +616,7 @@ static cudaError_t launch_mixed_one(const FrameArgs& a, cudaStream_t s) {
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const int need = (a.K + G::NG - 1) / G::NG;
-    const int grid = need < sms ? need : sms;
+    const int grid = a.K < sms ? a.K : sms;
     kern<<<grid, G::NT, G::SMEM, s>>>(a);
     return cudaGetLastError();
 }
