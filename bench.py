@@ -5,11 +5,16 @@ an end-to-end figure through the C ABI with host buffers, and the FP64 oracle
 timed on the host cores as a reported CPU baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload fermat|raster256|batch|batch-small]
+                  [--workload fermat|raster256|batch|batch-small] [--no-mixed]
+                  [--copy-streams S]
 
 --workload raster256 times the large scan instead: a 100 x 100 raster of
 256^2 frames (step 24 +-1 px) over a 3072^2 object, Poisson 10^8 photons,
 fixed probe.
+
+For 128^2 workloads the line also carries "mixed": the same steps with the
+frame DFTs as FP16 (per-frame scaled) and BF16x3 tensor-core contractions,
+each with its frame-kernel time, HBM fraction and tensor rate.
 
 Prints one JSON line on rank 0.  Under torchrun (N > 1) every rank runs an
 independent replica of the scan (the path has no exchange step on one box),
