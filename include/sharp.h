@@ -98,8 +98,9 @@ void sharp_default_params(sharp_params* p);
  * that touch each image block (Sec. 2.3) are built here once, on the host.
  * With a tensor-core precision mode the plan also holds the DFT matrix parts
  * (64 KB for FP16S, 128 KB for BF16X3).
- * Errors: INVALID_ARG (K < 1, ny or nx < m, bad position, unknown precision),
- * UNSUPPORTED_SIZE (m without a kernel, or a tensor-core mode with m != 128).
+ * Errors: INVALID_ARG (K < 1, ny or nx < m, bad position, beta outside
+ * (0.5, 1], unknown precision), UNSUPPORTED_SIZE (m without a kernel, or a
+ * tensor-core mode with m != 128).
  */
 int sharp_plan_create(sharp_plan* plan, int K, int m, int ny, int nx,
                       const int32_t* pos, const sharp_params* params,
@@ -266,8 +267,10 @@ int sharp_amp_loss_backward(sharp_plan plan, const float2* obj, const float2* pr
  * probe and metrics may be NULL); rebinding drops the recorded graphs.
  * sharp_batch_tuned_grid returns the grid chosen for frame size m (or -1).
  * sharp_batch_status synchronises `stream` and returns SHARP_ERR_TIMEOUT
- * (once) if a bounded wait of a batched frame pass gave up; the affected
- * scan's plan reports it through sharp_plan_status as well.
+ * (once) if a bounded wait of a batched frame pass gave up, or
+ * SHARP_ERR_INVALID_ARG if a scan's measured amplitudes hold a value that is
+ * not finite and non-negative; the affected scan's plan reports it through
+ * sharp_plan_status as well.
  * Errors: INVALID_ARG, STATE (unbound scan, diverging schedules), CUDA.
  */
 typedef struct sharp_batch_s* sharp_batch;
@@ -304,10 +307,33 @@ int sharp_fourier_project_noalloc(const float2* z, const float* amp, float2* out
 
 /*
  * Synchronise `stream` and report a sticky device-side failure of the plan's
- * kernels: SHARP_ERR_TIMEOUT when a bounded wait for a bulk copy gave up
- * (the affected step's results are invalid).  Clears the flag.
+ * kernels, then clear it:
+ *   SHARP_ERR_TIMEOUT     a bounded wait for a bulk copy or for tensor-core
+ *                         work gave up (the affected step's results are invalid);
+ *   SHARP_ERR_INVALID_ARG a frame pass read a measured amplitude that is not
+ *                         finite and non-negative (Eq. 1: a = |F z|), or the
+ *                         probe gives no finite positive illumination Q*Q
+ *                         anywhere (all zero or not finite; sharp_raar_init,
+ *                         probe updates, sharp_overlap_project).
+ * The first error raised since the last call is reported.
  */
 int sharp_plan_status(sharp_plan plan, cudaStream_t stream);
+
+/*
+ * Poll limit of the bounded device-side waits of the plan's frame passes
+ * (the first wait for each bulk copy of frame data and for each group of
+ * tensor-core MMAs).  Not part of the method: a watchdog setting.
+ *   polls < 0 : the default, 2^26 polls (seconds of waiting);
+ *   polls = 0 : no polling, so every such wait gives up at once (a frame
+ *               pass then stops early and sharp_plan_status reports
+ *               SHARP_ERR_TIMEOUT; used to exercise the error path);
+ *   polls > 0 : that many polls (at most 2^32 - 2).
+ * Whatever the setting, a kernel whose wait gave up waits with the default
+ * limit for its own copies and MMAs still in flight before it exits, and
+ * releases its tensor memory.  Applies to the launches queued after the call.
+ * Errors: INVALID_ARG.
+ */
+int sharp_plan_set_wait_limit(sharp_plan plan, long long polls);
 
 /*
  * Kernel timing (tracing aid; the paper reports per-kernel time shares in the

@@ -20,7 +20,8 @@ __all__ = [
     "sharp_overlap_project", "sharp_probe_update", "sharp_raar_init", "sharp_raar_step",
     "sharp_solution_error", "sharp_forward_amplitudes", "sharp_amp_loss",
     "sharp_amp_loss_backward", "AmpLoss", "amp_loss", "sharp_plan_set_profiling",
-    "sharp_plan_kernel_times", "sharp_plan_status", "sharp_fourier_project_noalloc", "Batch",
+    "sharp_plan_kernel_times", "sharp_plan_status", "sharp_plan_set_wait_limit", "sharp_fourier_project_noalloc",
+    "Batch",
     "SHARP_PROBE_CONSTRAINT_NONE", "SHARP_PROBE_CONSTRAINT_MASK", "SHARP_PROBE_CONSTRAINT_AMPLITUDE",
     "SHARP_PREC_FP32", "SHARP_PREC_FP16S", "SHARP_PREC_BF16X3", "PRECISIONS",
 ]
@@ -78,6 +79,7 @@ _lib_fns = {
     "sharp_amp_loss_backward": ([_P, _P, _P, _P, _D, _P, _P, _P], _I),
     "sharp_plan_set_profiling": ([_P, _I], _I),
     "sharp_plan_status": ([_P, _P], _I),
+    "sharp_plan_set_wait_limit": ([_P, ctypes.c_longlong], _I),
     "sharp_fourier_project_noalloc": ([_P, _P, _P, _P, _I, _I, _P], _I),
     "sharp_plan_set_probe_refinement": ([_P, _I, _P, _I, _P], _I),
     "sharp_probe_refine": ([_P, _P, _P, _P], _I),
@@ -231,6 +233,10 @@ def sharp_plan_status(plan, stream=None) -> None:
     _check(_C["sharp_plan_status"](plan, _stream(stream)))
 
 
+def sharp_plan_set_wait_limit(plan, polls: int) -> None:
+    _check(_C["sharp_plan_set_wait_limit"](plan, int(polls)))
+
+
 def sharp_plan_set_profiling(plan, enable: bool) -> None:
     _check(_C["sharp_plan_set_profiling"](plan, int(bool(enable))))
 
@@ -278,8 +284,13 @@ class Plan:
             pass
 
     def status(self, stream=None):
-        """Raise SharpError if a bounded device-side wait of this plan gave up."""
+        """Raise SharpError if a kernel of this plan flagged a failure (a bounded
+        wait gave up, or invalid amplitudes or probe were seen)."""
         _check(_C["sharp_plan_status"](self.handle, _stream(stream)))
+
+    def set_wait_limit(self, polls=-1):
+        """Poll limit of the frame passes' bounded waits (-1: default, 0: give up at once)."""
+        _check(_C["sharp_plan_set_wait_limit"](self.handle, int(polls)))
 
     # ---------------------------------------------------------- operators
     def q_gather(self, obj, probe):

@@ -137,10 +137,9 @@ __device__ __forceinline__ void form_row(const FrameArgs& a, int py, int px, siz
                 wf[n - n0] = ld_hint(a.w_form + y * M + x, pol_keep);
                 yv[n - n0] = a.psiy[o];
                 cv[n - n0] = ld_hint(a.c + fo + y * M + x, pol_stream);
-                if constexpr (FLAGS & RF_METRIC) {
-                    pv[n - n0] = a.psi[o];
+                if constexpr (FLAGS & (RF_METRIC | RF_FORM_B)) pv[n - n0] = a.psi[o];
+                if constexpr (FLAGS & RF_METRIC)
                     ev[n - n0] = a.read_e ? ld_hint(a.ebuf + fo + y * M + x, pol_stream) : make_float2(0.f, 0.f);
-                }
             }
 #pragma unroll
             for (int n = n0; n < n0 + CH; ++n) {
@@ -158,7 +157,9 @@ __device__ __forceinline__ void form_row(const FrameArgs& a, int py, int px, siz
                 for (int n = n0; n < n0 + CH; ++n) {
                     const int x = 16 * n + j;
                     const int o = obj_index(py, px, y, x, a.ny, a.nx, a.wrap);
-                    red_add_f2(a.accB + o, cmulc(ld_hint(a.w_proj + y * M + x, pol_keep), v[n]));
+                    // B' = Q*(z - w psi), relative to the object (image pass)
+                    const float2 wp = ld_hint(a.w_proj + y * M + x, pol_keep);
+                    red_add_f2(a.accB + o, cmulc(wp, csub(v[n], cmul(wp, pv[n - n0]))));
                 }
             }
             if (a.write_e) {
@@ -183,9 +184,10 @@ __device__ __forceinline__ void form_row(const FrameArgs& a, int py, int px, siz
 
 // Pass 2: the Fourier-domain step on column x, v[q] = X[16 q + j][x] (raw
 // DFT, m times the unitary transform).  AMPS and LOSS need no inverse.
+// `bad` collects measured amplitudes that are not finite and non-negative.
 template <int MODE>
 __device__ __forceinline__ void fourier_col(const FrameArgs& a, size_t fo, int x, int j, float2 (&v)[16],
-                                            float (&acc)[5]) {
+                                            float (&acc)[5], int& bad) {
     const float inv_m = 1.0f / M;
     if constexpr (MODE == MODE_AMPS) {
 #pragma unroll
@@ -209,9 +211,10 @@ __device__ __forceinline__ void fourier_col(const FrameArgs& a, size_t fo, int x
         for (int q = 0; q < 16; ++q) {
             float2& X = v[q];
             const float m2 = cabs2(X);
-            const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
+            const float rs = m2 > 0.f ? (MODE == MODE_RAAR ? rsqrt_refined(m2) : rsqrtf(m2)) : 0.f;
             const float d = av[q] - m2 * rs * inv_m;
             acc[0] += d * d;
+            bad |= (int)bad_amplitude(av[q]);
             if constexpr (MODE == MODE_RAAR) {
                 // ((1-2b) a Z/|Z| + b Z)/m on the unitary scale: the raw
                 // inverse returns c_new = (1-2b) P_a z + b z
@@ -235,15 +238,22 @@ __device__ __forceinline__ void finish_row(const FrameArgs& a, int py, int px, s
 #pragma unroll
     for (int n0 = 0; n0 < 16; n0 += CH) {
         if constexpr (MODE == MODE_RAAR) {
-            float2 wp[CH];
+            // C' += conj(w) (c_new - (1-b) w psi): overlap sum relative to the
+            // object (image pass)
+            const float rho = 1.f - a.beta;
+            float2 wp[CH], pv[CH];
 #pragma unroll
-            for (int n = n0; n < n0 + CH; ++n) wp[n - n0] = ld_hint(a.w_proj + y * M + 16 * n + j, pol_keep);
+            for (int n = n0; n < n0 + CH; ++n) {
+                const int x = 16 * n + j;
+                wp[n - n0] = ld_hint(a.w_proj + y * M + x, pol_keep);
+                pv[n - n0] = a.psi[obj_index(py, px, y, x, a.ny, a.nx, a.wrap)];
+            }
 #pragma unroll
             for (int n = n0; n < n0 + CH; ++n) {
                 const int x = 16 * n + j;
                 const int o = obj_index(py, px, y, x, a.ny, a.nx, a.wrap);
                 st_hint(a.c + fo + y * M + x, v[n], pol_stream);
-                red_add_f2(a.accA + o, cmulc(wp[n - n0], v[n]));
+                red_add_f2(a.accA + o, cmulc(wp[n - n0], csub(v[n], cscale(cmul(wp[n - n0], pv[n - n0]), rho))));
                 if (a.write_e) red_hint(a.ebuf + fo + y * M + x, v[n], pol_stream);
             }
         } else if constexpr (MODE == MODE_PROJECT || MODE == MODE_MASK) {
@@ -295,8 +305,14 @@ __global__ void __launch_bounds__(NT, 1) big_kernel(const FrameArgs ap, const Ba
     double accd[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     int loaded = batch ? -1 : 0;
     int eb = 0;
+    int bad = 0;
 
     auto flush = [&]() {   // block-wide
+        if (__syncthreads_or(bad) && tid == 0) {
+            raise_error(a.err, SHARP_ERR_INVALID_ARG);   // the scan's plan status
+            if (batch) raise_error(bt.err, SHARP_ERR_INVALID_ARG);
+        }
+        bad = 0;
         float s[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -362,7 +378,7 @@ __global__ void __launch_bounds__(NT, 1) big_kernel(const FrameArgs ap, const Ba
             for (int n = 0; n < 16; ++n) v[n] = ld_hint(scr + (16 * n + jc) * M + x, pol_keep);
             col_fwd(v, Ebuf + eb * E_ELEMS, tw, cx, jc);
             eb ^= 1;
-            fourier_col<MODE>(a, fo, x, jc, v, acc);
+            fourier_col<MODE>(a, fo, x, jc, v, acc, bad);
             if constexpr (MODE != MODE_AMPS && MODE != MODE_LOSS) {
                 col_inv(v, Ebuf + eb * E_ELEMS, tw, cx, jc);
                 eb ^= 1;

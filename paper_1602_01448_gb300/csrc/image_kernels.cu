@@ -4,8 +4,8 @@
 //
 // Q* and Q*Q are gathered per 32 x 32 image tile over the list of frames that
 // touch the tile (built once per plan), so every image pixel is written by
-// exactly one thread: no atomics, a fixed summation order, and compensated
-// (Kahan) FP32 sums.
+// exactly one thread: no atomics and a fixed summation order; Q*Q is summed
+// in FP64 across groups of FP32 terms, Q* z with compensated (Kahan) FP32.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -42,7 +42,10 @@ __global__ void w2_kernel(const float2* __restrict__ w, float* __restrict__ w2, 
 
 // Frame list entries of a tile staged in shared memory per round.
 constexpr int GATHER_STAGE = 512;
-// Frames summed in plain FP32 before each compensated (Kahan) add.
+// Frames summed in plain FP32 before each FP64 add: D = Q*Q (Eq. 9) is
+// accumulated in FP64 across groups (GB300's FP64 rate is low, so the per-term
+// adds stay FP32) and rounded once to FP32; near the probe edges, where D is
+// small and built from many tiny terms, that keeps it correctly rounded.
 constexpr int GATHER_GROUP = 16;
 
 template <int WRAP>
@@ -54,7 +57,7 @@ illum_gather_kernel(const int32_t* __restrict__ pos, const int* __restrict__ tpt
     const int tile = blockIdx.x;
     const int gx = (tile % tiles_x) * TILE + (threadIdx.x & 31);
     const int gy0 = (tile / tiles_x) * TILE + (threadIdx.x >> 5);
-    float s[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
+    double s[4] = {0.0, 0.0, 0.0, 0.0};        // FP64 sums of the FP32 group sums
     const int j0 = tptr[tile], j1 = tptr[tile + 1];
     for (int base = j0; base < j1; base += GATHER_STAGE) {
         const int n = min(GATHER_STAGE, j1 - base);
@@ -83,7 +86,7 @@ illum_gather_kernel(const int32_t* __restrict__ pos, const int* __restrict__ tpt
                 }
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r) kahan_add(s[r], cc[r], part[r]);
+            for (int r = 0; r < 4; ++r) s[r] += (double)part[r];
         }
     }
     float mx = 0.f;
@@ -91,8 +94,9 @@ illum_gather_kernel(const int32_t* __restrict__ pos, const int* __restrict__ tpt
     for (int r = 0; r < 4; ++r) {
         const int gy = gy0 + 8 * r;
         if (gy < ny && gx < nx) {
-            D[gy * nx + gx] = s[r];
-            mx = fmaxf(mx, s[r]);
+            const float d = (float)s[r];
+            D[gy * nx + gx] = d;
+            mx = fmaxf(mx, d);
         }
     }
 #pragma unroll
@@ -100,9 +104,15 @@ illum_gather_kernel(const int32_t* __restrict__ pos, const int* __restrict__ tpt
     if ((threadIdx.x & 31) == 0) atomicMax(dmax_bits, __float_as_uint(mx));
 }
 
+// 1/D above the threshold of reading R4, 0 below it.  A probe with no finite
+// positive illumination anywhere (zero, or not finite) leaves every frame
+// without an object pixel: that raises SHARP_ERR_INVALID_ARG on `err`.
 __global__ void invd_kernel(const float* __restrict__ D, float* __restrict__ invD,
-                            const unsigned* __restrict__ dmax_bits, int n) {
-    const float thr = 1e-12f * __uint_as_float(*dmax_bits);
+                            const unsigned* __restrict__ dmax_bits, int n, int* __restrict__ err) {
+    const float dmax = __uint_as_float(*dmax_bits);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !(dmax > 0.f && dmax <= 3.402823466e38f))
+        raise_error(err, SHARP_ERR_INVALID_ARG);
+    const float thr = 1e-12f * dmax;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float d = D[i];
         invD[i] = d > thr ? 1.0f / d : 0.0f;
@@ -165,11 +175,19 @@ __global__ void q_gather_kernel(const int32_t* __restrict__ pos, const float2* _
 }
 
 // ------------------------------------------------------------------ RAAR image pass
-// The frame pass scattered C = Q* c_new = (1-2b) A + b B (and B = Q* z after a
-// probe change).  Per pixel with D above the threshold:
-//   B/D = accB/D after a probe change, else the previous object psi;
-//   A/D = (C/D - b B/D) / (1-2b);  psi <- A/D;  psi_y <- 2b A/D - b B/D;
-// both 0 below the threshold; the sums are cleared for the next step.
+// The frame pass scattered its overlap sums relative to the object psi of
+// the previous step (the image this kernel overwrites):
+//   C' = Q*(c_new - (1-b) w psi)   with c_new = (1-2b) P_a z + b z,
+//   B' = Q*(z - w psi)             only after a probe change; otherwise
+//                                   Q* z = D psi exactly and B' = 0.
+// Then C = Q* c_new = C' + (1-b) D psi and B = Q* z = B' + D psi, so with
+// A = Q* P_a z = (C - b B)/(1-2b) (Sec. 2.2 RAAR update, Luke form):
+//   A/D   = psi + (C' - b B') / ((1-2b) D)          -> psi (Eq. 9)
+//   psi_y = (2b A - b B)/D = b psi + 2b (A/D - psi) - b B'/D
+// Only the corrections C', B' pass through the 1/(1-2b) factor, so FP32
+// rounding of the overlap sums is not amplified from full-size values.
+// Both images are 0 where D is below the threshold; the sums are cleared
+// for the next step.
 __global__ void normalise_kernel(float2* __restrict__ C, float2* __restrict__ B,
                                  const float* __restrict__ invD, float2* __restrict__ psiy,
                                  float2* __restrict__ psi, float beta, int form_b, int n) {
@@ -177,12 +195,17 @@ __global__ void normalise_kernel(float2* __restrict__ C, float2* __restrict__ B,
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float id = invD[i];
         const float2 cs = C[i];
+        const float2 bs = form_b ? B[i] : make_float2(0.f, 0.f);
         float2 ny_ = make_float2(0.f, 0.f), np_ = make_float2(0.f, 0.f);
         if (id > 0.f) {
-            const float2 bn = form_b ? cscale(B[i], id) : psi[i];
-            const float2 an = make_float2(k * fmaf(cs.x, id, -beta * bn.x), k * fmaf(cs.y, id, -beta * bn.y));
-            np_ = an;
-            ny_ = make_float2(fmaf(2.f * beta, an.x, -beta * bn.x), fmaf(2.f * beta, an.y, -beta * bn.y));
+            const float2 ps = psi[i];
+            const float kd = k * id;
+            // dA = A/D - psi
+            const float2 dA = make_float2(kd * fmaf(-beta, bs.x, cs.x), kd * fmaf(-beta, bs.y, cs.y));
+            np_ = cadd(ps, dA);
+            const float2 bd = cscale(bs, id);
+            ny_ = make_float2(fmaf(beta, ps.x, beta * fmaf(2.f, dA.x, -bd.x)),
+                              fmaf(beta, ps.y, beta * fmaf(2.f, dA.y, -bd.y)));
         }
         psi[i] = np_;
         psiy[i] = ny_;
@@ -544,7 +567,7 @@ cudaError_t launch_illumination(const Plan& p, const float2* w, float* w2, float
     cudaError_t e = illum_for(p, w, w2, D, dmax_bits, s);
     if (e != cudaSuccess) return e;
     const int n = p.ny * p.nx;
-    invd_kernel<<<grid_for(n, 256), 256, 0, s>>>(D, invD, dmax_bits, n);
+    invd_kernel<<<grid_for(n, 256), 256, 0, s>>>(D, invD, dmax_bits, n, p.errflag);
     return cudaGetLastError();
 }
 

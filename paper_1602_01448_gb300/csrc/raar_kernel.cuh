@@ -5,13 +5,18 @@
 //   Z   = F z                                             Eq. 2
 //   Z'  = a Z/|Z|                                         P_a (Eq. 7); eps_a partials
 //   c_i <- F* [(1-2b) Z' + b Z] = (1-2b) P_a z + b z       RAAR state
-//   C(r + x_i) += conj(w) c_i                             Q* of the new state
+//   C'(r + x_i) += conj(w) (c_i - (1-b) w psi(r + x_i))    Q* of the new state,
+//                                                          relative to the object
 // Because c_new = (1-2b) P_a z + b z, Q* c_new = (1-2b) A + b B with
-// A = Q* P_a z and B = Q* z, so the image pass recovers A = (C - b B)/(1-2b)
-// and forms psi = A/D, psi_y = (2b A - b B)/D; B/D is the previous object
-// unless the probe changed (then B is scattered here from z).  Transforming
-// the combination instead of Z' alone means the epilogue needs neither the old
-// state nor a second gather: each frame is read once and written once.
+// A = Q* P_a z and B = Q* z, so the image pass recovers
+// A/D = psi + (C' - b B')/((1-2b) D) and psi_y = (2b A - b B)/D, where
+// B' = Q*(z - w psi) is zero unless the probe changed (then it is scattered
+// here from z).  The sums are taken relative to w psi so that near
+// convergence they hold small corrections: FP32 rounding of the overlap sums
+// then stays far below the step-to-step change instead of being amplified
+// by 1/|1-2b| from the full-size sums.  Transforming the combination instead
+// of Z' alone means the epilogue needs neither the old state nor the old
+// iterate: each frame is read once and written once.
 //
 // One persistent block per SM walks frames i = blockIdx.x + k * gridDim.x.
 // Frame i+1's state is copied by TMA (one cp.async.bulk of m^2 complex values)
@@ -69,10 +74,9 @@ __device__ __forceinline__ void raar_load_phase(const FrameArgs& a, int py, int 
             wf[k - k0] = ld_hint(a.w_form + y * M + x, pol_keep);
             yv[k - k0] = ld_hint(a.psiy + o, pol_keep);
             if constexpr (FLAGS & RF_FORM_B) wp[k - k0] = ld_hint(a.w_proj + y * M + x, pol_keep);
-            if constexpr (FLAGS & RF_METRIC) {
-                pv[k - k0] = ld_hint(a.psi + o, pol_keep);
+            if constexpr (FLAGS & (RF_METRIC | RF_FORM_B)) pv[k - k0] = ld_hint(a.psi + o, pol_keep);
+            if constexpr (FLAGS & RF_METRIC)
                 ev[k - k0] = a.read_e ? ld_hint(a.ebuf + fo + y * M + x, pol_stream) : make_float2(0.f, 0.f);
-            }
         }
 #pragma unroll
         for (int k = k0; k < k0 + CH; ++k) {
@@ -91,7 +95,7 @@ __device__ __forceinline__ void raar_load_phase(const FrameArgs& a, int py, int 
             for (int k = k0; k < k0 + CH; ++k) {
                 const int y = q + TX * k;
                 const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
-                red_hint(a.accB + o, cmulc(wp[k - k0], v[k]), pol_keep);
+                red_hint(a.accB + o, cmulc(wp[k - k0], csub(v[k], cmul(wp[k - k0], pv[k - k0]))), pol_keep);
             }
         }
         if (a.write_e) {
@@ -106,10 +110,11 @@ __device__ __forceinline__ void raar_load_phase(const FrameArgs& a, int py, int 
 }
 
 // Y = ((1-2b) a Z/|Z| + b Z) / m on the unitary scale (pass-3 layout), so the
-// raw inverse returns c_new directly; phase 1 where Z = 0.
+// raw inverse returns c_new directly; phase 1 where Z = 0.  `bad` collects
+// amplitudes that are not finite and non-negative.
 template <int M>
 __device__ __forceinline__ void raar_fourier_phase(const FrameArgs& a, size_t fo, float2 (&v)[32],
-                                                   float (&acc)[5]) {
+                                                   float (&acc)[5], int& bad) {
     using G = Fft3<M>;
     const float inv_m = 1.0f / M;
     const float b = a.beta;
@@ -123,16 +128,17 @@ __device__ __forceinline__ void raar_fourier_phase(const FrameArgs& a, size_t fo
     for (int j = 0; j < 32; ++j) {
         float2& X = v[j];
         const float m2 = cabs2(X);
-        const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
+        const float rs = m2 > 0.f ? rsqrt_refined(m2) : 0.f;
         const float d = av[j] - m2 * rs * inv_m;
         acc[0] += d * d;
         acc[1] += av[j] * av[j];
+        bad |= (int)bad_amplitude(av[j]);
         X = m2 > 0.f ? cscale(X, fmaf(cp * av[j], rs, b * inv_m) * inv_m)
                      : make_float2(cp * av[j] * inv_m, 0.f);
     }
 }
 
-// Store c_new and scatter C += conj(w_p) c_new (pass-1 layout).
+// Store c_new and scatter C' += conj(w_p) (c_new - (1-b) w_p psi) (pass-1 layout).
 template <int M, int WRAP>
 __device__ __forceinline__ void raar_epilogue(const FrameArgs& a, int py, int px, size_t fo, const float2 (&v)[32],
                                               uint64_t pol_stream, uint64_t pol_keep) {
@@ -140,18 +146,24 @@ __device__ __forceinline__ void raar_epilogue(const FrameArgs& a, int py, int px
     constexpr int CH = 8;
     const int q = threadIdx.x / M;
     const int x = threadIdx.x % M;
+    const float rho = 1.f - a.beta;
 #pragma unroll
     for (int k0 = 0; k0 < 32; k0 += CH) {
-        float2 wp[CH];
+        float2 wp[CH], pv[CH];
 #pragma unroll
-        for (int k = k0; k < k0 + CH; ++k) wp[k - k0] = ld_hint(a.w_proj + (q + TX * k) * M + x, pol_keep);
+        for (int k = k0; k < k0 + CH; ++k) {
+            const int y = q + TX * k;
+            wp[k - k0] = ld_hint(a.w_proj + y * M + x, pol_keep);
+            pv[k - k0] = ld_hint(a.psi + obj_index(py, px, y, x, a.ny, a.nx, WRAP), pol_keep);
+        }
 #pragma unroll
         for (int k = k0; k < k0 + CH; ++k) {
             const int y = q + TX * k;
             const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
             const float2 cn = v[k];
             st_hint(a.c + fo + y * M + x, cn, pol_stream);
-            red_hint(a.accA + o, cmulc(wp[k - k0], cn), pol_keep);
+            const float2 dn = csub(cn, cscale(cmul(wp[k - k0], pv[k - k0]), rho));
+            red_hint(a.accA + o, cmulc(wp[k - k0], dn), pol_keep);
             if (a.write_e) red_hint(a.ebuf + fo + y * M + x, cn, pol_stream);
         }
         chunk_fence_r();
@@ -208,9 +220,11 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
     int cur = s_next;
 
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    int bad = 0;
     unsigned par_c = 0;
     bool c_pending = cur < a.K;   // uniform across the block
     bool ok = true;
+    const unsigned polls = wait_polls(a.spin);
 
     while (cur < a.K) {
         const int i = cur;
@@ -223,7 +237,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
         if (tid == 0) bulk_prefetch_l2(a.amp + fo, (unsigned)(MM * sizeof(float)));
 
         // ---------------------------------------------- state arrives (TMA)
-        ok = __syncthreads_and(mbar_wait(&bars[0], par_c));
+        ok = __syncthreads_and(mbar_wait(&bars[0], par_c, polls));
         if (!ok) break;
         par_c ^= 1u;
         c_pending = false;
@@ -231,7 +245,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
 
         raar_load_phase<M, FLAGS, WRAP>(a, py, px, fo, S, v, acc, pol_stream, pol_keep);
         G::forward(v, S, tw);
-        raar_fourier_phase<M>(a, fo, v, acc);
+        raar_fourier_phase<M>(a, fo, v, acc, bad);
         G::inverse(v, S, tw);
 
         fence_proxy_async_smem();
@@ -245,12 +259,14 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
     }
 
     if (!ok) {
-        // A wait gave up: drain (bounded) whatever copies this block may still
-        // have in flight, flag the failure, and leave the sums alone.
+        // A wait gave up: drain (bounded, full limit) whatever copies this
+        // block may still have in flight, flag the failure, and leave the
+        // sums alone.
         if (c_pending) mbar_wait(&bars[0], par_c);
         if (tid == 0) atomicExch(a.err, SHARP_ERR_TIMEOUT);
         return;
     }
+    if (__syncthreads_or(bad) && tid == 0) raise_error(a.err, SHARP_ERR_INVALID_ARG);
     block_sum<NT, 5>(acc, red);
     if (tid == 0) {
 #pragma unroll
@@ -314,11 +330,17 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_batch_kerne
     int cur = s_next, cur_scan = s_next_scan, loaded_scan = -1;
 
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    int bad = 0;
     unsigned par_c = 0;
     bool c_pending = cur < bt.total;
     bool ok = true;
 
     auto flush = [&](int s) {                 // block-wide: metric sums to scan s
+        if (__syncthreads_or(bad) && tid == 0) {
+            raise_error(bt.scans[s].err, SHARP_ERR_INVALID_ARG);   // the scan's plan status
+            raise_error(bt.err, SHARP_ERR_INVALID_ARG);
+        }
+        bad = 0;
         block_sum<NT, 5>(acc, red);
         if (tid == 0) {
 #pragma unroll
@@ -348,7 +370,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_batch_kerne
         float2 v[32];
         if (tid == 0) bulk_prefetch_l2(sa.amp + fo, (unsigned)(MM * sizeof(float)));
 
-        ok = __syncthreads_and(mbar_wait(&bars[0], par_c));
+        ok = __syncthreads_and(mbar_wait(&bars[0], par_c, wait_polls(sa.spin)));
         if (!ok) break;
         par_c ^= 1u;
         c_pending = false;
@@ -357,7 +379,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_batch_kerne
         if (sa.wrap) raar_load_phase<M, FLAGS, 1>(sa, py, px, fo, S, v, acc, pol_stream, pol_keep);
         else raar_load_phase<M, FLAGS, 0>(sa, py, px, fo, S, v, acc, pol_stream, pol_keep);
         G::forward(v, S, tw);
-        raar_fourier_phase<M>(sa, fo, v, acc);
+        raar_fourier_phase<M>(sa, fo, v, acc, bad);
         G::inverse(v, S, tw);
 
         fence_proxy_async_smem();

@@ -133,6 +133,8 @@ struct MixCtx {
     uint64_t* bar;         // MMA completion
     float* s_max;          // one float per warp
     unsigned phase;
+    unsigned polls;        // poll limit of the first wait on each completion
+    bool mma_pending;      // a commit has not been waited for (uniform)
 };
 
 // Largest value over the block (all threads receive it).
@@ -259,8 +261,9 @@ __device__ __forceinline__ float mix_region_max(const MixCtx& x, uint32_t src) {
 // their later TMEM accesses after it.
 template <int PREC>
 __device__ __forceinline__ bool mix_wait(MixCtx& x) {
-    const bool ok = __syncthreads_and(x.leader ? mbar_wait(x.bar, x.phase) : true);
+    const bool ok = __syncthreads_and(x.leader ? mbar_wait(x.bar, x.phase, x.polls) : true);
     if (!ok) return false;
+    x.mma_pending = false;
     x.phase ^= 1u;
     tc_fence_after();
     return true;
@@ -286,6 +289,7 @@ __device__ __forceinline__ bool mix_stage(MixCtx& x, uint32_t src, uint32_t dst,
                 if (j == 1) mma_commit(x.bar);
             }
         }
+        x.mma_pending = true;
         return mix_wait<PREC>(x);
     } else {
 #pragma unroll
@@ -299,6 +303,7 @@ __device__ __forceinline__ bool mix_stage(MixCtx& x, uint32_t src, uint32_t dst,
                 mix_issue<PREC>(x.sA, x.sB, x.tbase + dst, j, inverse);
                 mma_commit(x.bar);
             }
+            x.mma_pending = true;
             if (!mix_wait<PREC>(x)) return false;
         }
         return true;
@@ -330,6 +335,8 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     x.bar = &bar;
     x.s_max = s_max;
     x.phase = 0;
+    x.polls = wait_polls(ap.spin);
+    x.mma_pending = false;
 
     {   // DFT matrix parts, already in the operand layout, into shared memory
         const uint4* src = reinterpret_cast<const uint4*>(ap.dft_tab);
@@ -365,6 +372,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     const float cp = 1.f - 2.f * b;
     const int xcol = x.r;   // frame column n2 owned by this thread
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    int bad = 0;   // an amplitude that is not finite and non-negative
     bool ok = true;
 
     // The frame inputs streamed from HBM (state or input frames, eps_Delta
@@ -411,7 +419,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
 
         // ------------------------------------------------ load: z into RA
         if constexpr (G::STAGE) {
-            ok = __syncthreads_and(mbar_wait(&cbar, cpar));
+            ok = __syncthreads_and(mbar_wait(&cbar, cpar, x.polls));
             if (!ok) break;
             cpar ^= 1u;
             st_pending = false;
@@ -434,11 +442,10 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                         wf[k] = ld_hint(a.w_form + y * M + xcol, pol_keep);
                         yv[k] = ld_hint(a.psiy + o, pol_keep);
                         if constexpr (FLAGS & RF_FORM_B) wp[k] = ld_hint(a.w_proj + y * M + xcol, pol_keep);
-                        if constexpr (FLAGS & RF_METRIC) {
-                            pv[k] = ld_hint(a.psi + o, pol_keep);
+                        if constexpr (FLAGS & (RF_METRIC | RF_FORM_B)) pv[k] = ld_hint(a.psi + o, pol_keep);
+                        if constexpr (FLAGS & RF_METRIC)
                             ev[k] = a.read_e ? ld_hint(a.ebuf + fo + y * M + xcol, pol_stream)
                                              : make_float2(0.f, 0.f);
-                        }
                     }
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
@@ -454,7 +461,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                         }
                         if constexpr (FLAGS & RF_FORM_B) {
                             const int o = obj_index(py, px, y, xcol, a.ny, a.nx, WRAP);
-                            red_hint(a.accB + o, cmulc(wp[k], z), pol_keep);
+                            red_hint(a.accB + o, cmulc(wp[k], csub(z, cmul(wp[k], pv[k]))), pol_keep);
                         }
                         if (a.write_e) st_hint(a.ebuf + fo + y * M + xcol, make_float2(-z.x, -z.y), pol_stream);
                     }
@@ -510,6 +517,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                         const float d = av[t] - m2 * rs;
                         acc[0] += d * d;
                         acc[1] += av[t] * av[t];
+                        bad |= (int)bad_amplitude(av[t]);
                         if (m2 > 0.f) {
                             const float f = fmaf(cp * av[t], rs, b);
                             ur[t] = X * f;
@@ -556,9 +564,14 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                     tmem_ld16x2(x.tl + RA + y0, x.tl + RA + 128 + y0, re, im);
                     if constexpr (RAAR) {
                         {
-                            float2 wp[16];
+                            // C' += conj(w) (c_new - (1-b) w psi), relative to the object
+                            const float rho = 1.f - a.beta;
+                            float2 wp[16], pv[16];
 #pragma unroll
-                            for (int k = 0; k < 16; ++k) wp[k] = ld_hint(a.w_proj + (y0 + k) * M + xcol, pol_keep);
+                            for (int k = 0; k < 16; ++k) {
+                                wp[k] = ld_hint(a.w_proj + (y0 + k) * M + xcol, pol_keep);
+                                pv[k] = ld_hint(a.psi + obj_index(py, px, y0 + k, xcol, a.ny, a.nx, WRAP), pol_keep);
+                            }
 #pragma unroll
                             for (int k = 0; k < 16; ++k) {
                                 const int t = k;
@@ -566,7 +579,8 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                                 const int o = obj_index(py, px, y, xcol, a.ny, a.nx, WRAP);
                                 const float2 cn = make_float2(re[t] * inv, im[t] * inv);
                                 st_hint(a.c + fo + y * M + xcol, cn, pol_stream);
-                                red_hint(a.accA + o, cmulc(wp[k], cn), pol_keep);
+                                red_hint(a.accA + o, cmulc(wp[k], csub(cn, cscale(cmul(wp[k], pv[k]), rho))),
+                                         pol_keep);
                                 if (a.write_e) red_hint(a.ebuf + fo + y * M + xcol, cn, pol_stream);
                             }
                         }
@@ -583,12 +597,16 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         // so the next frame's load phase may overwrite them in program order
     }
 
-    if (!ok && x.leader) mbar_wait(x.bar, x.phase);   // a wait gave up: wait (bounded) once more for the MMAs
-    if (st_pending && x.leader) mbar_wait(&cbar, cpar);   // and for a staging copy still in flight
+    // A wait gave up: wait (bounded, full limit) once more for MMAs whose
+    // commit was not waited for and for a staging copy still in flight, so
+    // that nothing writes TMEM or shared memory after the block has left.
+    if (x.mma_pending && x.leader) mbar_wait(x.bar, x.phase);
+    if (st_pending && x.leader) mbar_wait(&cbar, cpar);
     const bool all_ok = __syncthreads_and(ok);
     if (!all_ok) {
         if (tid == 0) atomicExch(a.err, SHARP_ERR_TIMEOUT);   // flag the failure, leave the sums alone
     } else {
+        if (__syncthreads_or(bad) && tid == 0) raise_error(a.err, SHARP_ERR_INVALID_ARG);
         block_sum<G::NT, 5>(acc, red);
         if (tid == 0) {
             if constexpr (RAAR) {

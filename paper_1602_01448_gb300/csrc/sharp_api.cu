@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "sharp_common.cuh"
+#include "tma.cuh"
 
 using sharp::Plan;
 
@@ -105,6 +106,7 @@ sharp::FrameArgs base_args(const Plan& p) {
     a.scratch = p.big_scratch;
     a.counter = p.counter;
     a.dft_tab = p.dft_tab;
+    a.spin = p.wait_spin;
     return a;
 }
 
@@ -283,7 +285,11 @@ int sharp_plan_create(sharp_plan* out, int K, int m, int ny, int nx, const int32
     sharp_params prm;
     sharp_default_params(&prm);
     if (params) prm = *params;
-    if (!(prm.beta > 0.f && prm.beta <= 1.f)) return fail(SHARP_ERR_INVALID_ARG, "beta = %g outside (0, 1]", prm.beta);
+    // RAAR's relaxation range (Sec. 2.2).  At b = 1/2 the new state
+    // (1-2b) P_a z + b z carries no trace of P_a z, and the image pass
+    // recovers Q* P_a z with the factor 1/(1-2b).
+    if (!(prm.beta > 0.5f && prm.beta <= 1.f))
+        return fail(SHARP_ERR_INVALID_ARG, "beta = %g outside (0.5, 1]", prm.beta);
     if (prm.probe_every < 0 || prm.residual_every < 0) return fail(SHARP_ERR_INVALID_ARG, "negative cadence");
     if (prm.precision != SHARP_PREC_FP32 && prm.precision != SHARP_PREC_FP16S && prm.precision != SHARP_PREC_BF16X3)
         return fail(SHARP_ERR_INVALID_ARG, "unknown precision %d", prm.precision);
@@ -401,8 +407,21 @@ int sharp_plan_status(sharp_plan plan, cudaStream_t s) {
     SHARP_CK(cudaStreamSynchronize(s));
     if (flag != 0) {
         SHARP_CK(cudaMemsetAsync(plan->p.errflag, 0, sizeof(int), s));
-        return fail(flag, "a bounded device-side wait gave up (the step's results are invalid)");
+        SHARP_CK(cudaStreamSynchronize(s));
+        if (flag == SHARP_ERR_TIMEOUT)
+            return fail(flag, "a bounded device-side wait gave up (the step's results are invalid)");
+        if (flag == SHARP_ERR_INVALID_ARG)
+            return fail(flag, "invalid data seen on the device: a measured amplitude that is not finite and "
+                              "non-negative, or a probe without finite positive illumination");
+        return fail(flag, "device-side error %d", flag);
     }
+    return SHARP_OK;
+}
+
+int sharp_plan_set_wait_limit(sharp_plan plan, long long polls) {
+    if (int r = check_plan(plan)) return r;
+    if (polls > 0xfffffffeLL) return fail(SHARP_ERR_INVALID_ARG, "wait limit %lld above 2^32 - 2 polls", polls);
+    plan->p.wait_spin = polls < 0 ? 0u : (polls == 0 ? sharp::kNoPolls : (unsigned)polls);
     return SHARP_OK;
 }
 

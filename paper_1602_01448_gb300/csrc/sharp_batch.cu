@@ -322,6 +322,8 @@ int sharp_batch_status(sharp_batch b, cudaStream_t stream) {
     if (e != cudaSuccess) return bfail(SHARP_ERR_CUDA, cudaGetErrorString(e));
     if (flag != 0) {
         cudaMemsetAsync(b->err, 0, sizeof(int), stream);
+        if (flag == SHARP_ERR_INVALID_ARG)
+            return bfail(flag, "a measured amplitude of a scan is not finite and non-negative");
         return bfail(flag, "a bounded device-side wait gave up (the step's results are invalid)");
     }
     return SHARP_OK;

@@ -26,6 +26,26 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 }
 __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 
+// A measured Fourier amplitude (Eq. 1: a = |F z| >= 0) that is NaN, infinite
+// or negative; the frame passes raise SHARP_ERR_INVALID_ARG on the plan.
+__device__ __forceinline__ bool bad_amplitude(float a) { return !(a >= 0.f && a <= 3.402823466e38f); }
+
+// Record a kernel-side error on a plan's flag unless one is already set.
+__device__ __forceinline__ void raise_error(int* err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+// 1/sqrt(x) for x > 0: the hardware estimate refined by one Newton step for
+// f(r) = r^-2 - x, r <- r + r (1 - x r^2) / 2, evaluated with a fused
+// multiply-add.  The result is within about one unit in the last place and
+// carries no systematic bias, so |P_a z| (Eq. 7) matches the measured
+// amplitude on average; a biased estimate shifts the RAAR fixed point.
+__device__ __forceinline__ float rsqrt_refined(float x) {
+    const float r = rsqrtf(x);
+    const float e = fmaf(-(x * r), r, 1.0f);
+    return fmaf(0.5f * r, e, r);
+}
+
 // Vector reductions into global memory (sm_90+): one red.global per pixel.
 __device__ __forceinline__ void red_add_f2(float2* p, float2 v) {
     atomicAdd(p, v);
@@ -89,8 +109,9 @@ struct Plan {
     float* Dsum;             // Q*Q (ny*nx), FP32 compensated sum
     float* invD;             // 1/D or 0 below the threshold
     unsigned* dmax_bits;     // max D as float bits
-    // overlap sums (float2 images): accA = Q* c_new (c_new the new frame
-    // state), accB = Q* z (only after a probe change)
+    // overlap sums (float2 images), relative to the current object psi:
+    // accA = Q*(c_new - (1-b) w psi) (c_new the new frame state), accB =
+    // Q*(z - w psi) (only after a probe change)
     float2* accA;
     float2* accB;
     bool b_valid;            // B/D equals the previous object (no probe change)
@@ -123,6 +144,8 @@ struct Plan {
     // tensor-core precision modes: the m x m DFT matrix parts in the operand
     // layout of the contraction kernels (nullptr in FP32 mode)
     void* dft_tab;
+    // poll limit of the frame passes' bounded waits (FrameArgs::spin encoding)
+    unsigned wait_spin;
 };
 
 constexpr int TILE = 32;
@@ -162,6 +185,7 @@ struct FrameArgs {
     int* counter;            // frame counter of the persistent RAAR pass (zeroed per launch)
     float2* scratch;         // 256^2 frames: one m*m slab per block of the frame kernels
     const void* dft_tab;     // tensor-core precision modes: DFT matrix parts (raar_mixed.cuh layout)
+    unsigned spin;           // poll limit of the first bounded waits (wait_polls: 0 default, kNoPolls none)
 };
 
 // compile-time flags of MODE_RAAR

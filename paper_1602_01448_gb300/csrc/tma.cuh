@@ -1,7 +1,10 @@
 // Bulk asynchronous copies (TMA, cp.async.bulk) into shared memory with
 // mbarrier completion, for sm_90+ (written for sm_103a).  Every wait is
-// bounded: after kSpinLimit polls it gives up and reports failure so that the
+// bounded: after a number of polls (kSpinLimit unless the plan sets another
+// limit for its first waits) it gives up and reports failure so that the
 // kernel can flag SHARP_ERR_TIMEOUT and return instead of hanging the GPU.
+// After a wait gave up, a kernel drains the copies and tensor-core work it
+// still has in flight with the full limit before it exits.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -10,6 +13,13 @@
 namespace sharp {
 
 constexpr unsigned kSpinLimit = 1u << 26;   // polls before a wait gives up (~seconds)
+constexpr unsigned kNoPolls = 0xffffffffu;  // FrameArgs::spin value: give up without polling
+
+// Poll limit of a kernel's first waits from FrameArgs::spin: 0 selects the
+// default kSpinLimit, kNoPolls none at all (every such wait gives up).
+__host__ __device__ __forceinline__ unsigned wait_polls(unsigned spin) {
+    return spin == 0 ? kSpinLimit : (spin == kNoPolls ? 0u : spin);
+}
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -41,9 +51,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     return ok != 0;
 }
 
-// Bounded wait for phase `parity` of `bar`; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-    for (unsigned it = 0; it < kSpinLimit; ++it)
+// Bounded wait for phase `parity` of `bar`; false if it gave up after
+// `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned limit = kSpinLimit) {
+    for (unsigned it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

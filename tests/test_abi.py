@@ -68,5 +68,19 @@ def test_plan_create_rejects_bad_arguments_on_host(lib):
     assert f(ctypes.byref(h), 4, 64, 32, 256, dummy, None, None) == 1       # object smaller than frame
     assert f(ctypes.byref(h), 4, 96, 256, 256, dummy, None, None) == 2      # no kernel for m=96
     assert f(ctypes.byref(h), 4, 64, 256, 256, None, None, None) == 1       # NULL positions
+
+    class Params(ctypes.Structure):
+        _fields_ = [("beta", ctypes.c_float), ("wrap", ctypes.c_int), ("probe_every", ctypes.c_int),
+                    ("residual_every", ctypes.c_int), ("precision", ctypes.c_int)]
+    # RAAR's relaxation range is (0.5, 1] (Sec. 2.2): at 1/2 the new state
+    # carries no trace of P_a z, below it the method is not RAAR
+    for beta in (0.5, 0.3, 0.0, -1.0, 1.01, float("nan")):
+        p = Params()
+        lib.sharp_default_params(ctypes.byref(p))
+        p.beta = beta
+        assert f(ctypes.byref(h), 4, 64, 256, 256, dummy, ctypes.byref(p), None) == 1, beta
+        assert b"beta" in lib.sharp_last_error()
     lib.sharp_plan_destroy.argtypes = [ctypes.c_void_p]
     assert lib.sharp_plan_destroy(None) == 0
+    lib.sharp_plan_set_wait_limit.argtypes = [ctypes.c_void_p, ctypes.c_longlong]
+    assert lib.sharp_plan_set_wait_limit(None, 5) == 1                        # NULL plan

@@ -105,23 +105,49 @@ def test_residual_cadence_and_nan_off_cadence():
             assert np.isnan(met[1]) and np.isnan(met[2])
 
 
-@pytest.mark.parametrize("beta", [1.0, 0.55])
-def test_raar_beta_extremes_match_oracle(beta):
+def _beta_tolerance(beta, steps, e_op=1e-5):
+    """Parity bound of a RAAR run with relaxation beta after `steps` steps.
+
+    The image pass forms A/D = psi + (C' - b B')/((1-2b) D) from the FP32
+    frame pass (Sec. 2.2 RAAR update, Luke form): an error of e_op (the FP32
+    single-operator bound) in the frame-pass sums reaches the object once
+    directly and once through the factor 1/|1-2b|, and the errors of
+    successive steps add: steps * (1 + 1/|1-2b|) * e_op."""
+    return steps * (1.0 + 1.0 / abs(1.0 - 2.0 * beta)) * e_op
+
+
+@pytest.mark.parametrize("beta", [1.0, 0.75, 0.55, 0.51])
+def test_raar_beta_range_matches_oracle(beta):
     # beta = 1 is Douglas-Rachford (2 P_Q P_a - P_Q - P_a + I); beta near 1/2
-    # makes 1/(1-2b) in the image pass large
+    # makes 1/(1-2b) in the image pass large (51 at beta = 0.51)
     S = _lib()
     obj, w, pos, shape, a = _noisy_scan(64, 4, 12, 21, seed=13)
     psi0 = synth.random_object(shape, np.random.default_rng(14), phase_sigma=1.0)
-    ref = O.raar_reconstruct(a, pos, shape, w, psi0, 3, beta=beta)
+    n_steps = 3
+    ref = O.raar_reconstruct(a, pos, shape, w, psi0, n_steps, beta=beta)
     plan = S.Plan(pos, 64, shape, beta=beta, residual_every=1)
     plan.raar_init(dev(psi0), dev(w))
     ta = dev(a, torch.float32)
-    for step_i in range(3):
+    for step_i in range(n_steps):
         met = host(plan.raar_step(ta)).real
-        _check_metrics(met, ref["history"][step_i], step_i == 0)
+        rec = ref["history"][step_i]
+        tol = max(1e-4, _beta_tolerance(beta, step_i + 1))
+        for j, key in enumerate(("eps_a", "eps_q", "eps_delta")):
+            assert abs(met[j] - rec[key]) <= tol * rec[key] + 2e-6, (step_i, key, met[j], rec[key])
     D = O.illumination(w, pos, shape)
     vis = D > 1e-3 * D.max()
-    assert rel_l2(host(plan.psi), ref["psi"], vis) < 1e-4 * (1 + 4 * (beta < 0.6))
+    err = rel_l2(host(plan.psi), ref["psi"], vis)
+    print(f"beta {beta}: object rel err {err:.2e} after {n_steps} steps (bound {_beta_tolerance(beta, n_steps):.1e})")
+    assert err < _beta_tolerance(beta, n_steps)
+
+
+def test_beta_at_one_half_is_rejected():
+    S = _lib()
+    pos = np.array([[0, 0], [8, 8]], np.int32)
+    for beta in (0.5, 0.25):
+        with pytest.raises(S.SharpError) as ei:
+            S.Plan(pos, 64, (80, 80), beta=beta)
+        assert ei.value.code == 1 and "beta" in str(ei.value)
 
 
 def test_single_frame_scan_matches_oracle():
@@ -162,12 +188,10 @@ def test_exact_data_is_a_fixed_point_on_gpu():
 
 
 def test_small_raster_nrmse_within_2_percent_of_oracle():
-    # 100 frames of 64^2, 256^2 object, noiseless, known probe, 100 iterations.
-    # eps_0 of the GPU object tracks the oracle's within 1.02x at every
-    # checkpoint where the oracle's eps_0 is above 1e-6; at iteration 100 the
-    # oracle sits at ~5e-7, within 4x of the FP32 pipeline's rounding floor
-    # (~1.2e-7, reproduced by a float32 CPU emulation), where the ratio is
-    # rounding noise (observed 1.00-1.05): bounded at 1.10 there.
+    # 100 frames of 64^2, 256^2 object, noiseless, known probe, 100
+    # iterations: eps_0 (Eq. 14) of the GPU object stays within 1.02x of the
+    # FP64 oracle's at every 10th iteration, iteration 100 included (the
+    # oracle reaches ~4.9e-7 there).
     S = _lib()
     s = synth.scan_small_raster()
     a = O.forward_amplitudes(s.obj, s.probe, s.pos).astype(np.float32).astype(np.float64)
@@ -186,11 +210,9 @@ def test_small_raster_nrmse_within_2_percent_of_oracle():
             ratios[it] = e_gpu / e_ref[it - 1]
     e_host = O.eps_0_object(host(plan.psi), s.obj, s.probe, s.pos, s.shape)
     assert abs(e_gpu - e_host) < 1e-3 * e_host + 1e-9
-    for it, r in ratios.items():
-        if e_ref[it - 1] > 1e-6:
-            assert r <= 1.02, (it, r, ratios)
-    assert ratios[100] <= 1.10, ratios
     print("eps_0 ratio GPU/oracle by iteration:", {k: round(v, 4) for k, v in ratios.items()})
+    for it, r in ratios.items():
+        assert r <= 1.02, (it, r, ratios)
 
 
 def _host_amplitudes(s, seed, chunk=500):
