@@ -189,6 +189,44 @@ def test_eps_q_by_hand():
     assert abs(O.eps_q(z, a, s.probe, s.pos, s.shape) - expect) < 1e-12
 
 
+def test_object_nrmse_by_hand():
+    # The secondary object report (reading R8): over the pixels whose
+    # illumination D = Q*Q reaches 10 % of its maximum, the relative error of
+    # psi against psi_true after the closed-form global phase.  Written out
+    # with explicit loops over the frame windows and the selected pixels.
+    s = synth.scan_tiny(seed=12)
+    rng = np.random.default_rng(31)
+    psi = s.obj * np.exp(0.7j) + 0.05 * (rng.standard_normal(s.shape) + 1j * rng.standard_normal(s.shape))
+    D = np.zeros(s.shape)
+    for r0, c0 in s.pos:
+        for y in range(s.m):
+            for x in range(s.m):
+                D[r0 + y, c0 + x] += abs(s.probe[y, x]) ** 2
+    dmax = max(D.ravel())
+    num = 0j
+    pairs = []
+    for y in range(s.shape[0]):
+        for x in range(s.shape[1]):
+            if D[y, x] >= 0.1 * dmax:
+                num += np.conj(psi[y, x]) * s.obj[y, x]
+                pairs.append((psi[y, x], s.obj[y, x]))
+    ph = num / abs(num)
+    err = np.sqrt(sum(abs(ph * u - v) ** 2 for u, v in pairs))
+    ref = np.sqrt(sum(abs(v) ** 2 for _, v in pairs))
+    got = O.object_nrmse(psi, s.obj, s.probe, s.pos, s.shape)
+    assert abs(got - err / ref) < 1e-12
+    # pixels below the threshold do not count: changing them leaves it unchanged
+    low = D < 0.1 * dmax
+    assert low.any()
+    psi2 = np.where(low, 123.0 + 4j, psi)
+    assert abs(O.object_nrmse(psi2, s.obj, s.probe, s.pos, s.shape) - got) < 1e-14
+    # and one pixel just above the threshold does
+    hi = np.argwhere(~low)[0]
+    psi3 = psi.copy()
+    psi3[tuple(hi)] += 1.0
+    assert abs(O.object_nrmse(psi3, s.obj, s.probe, s.pos, s.shape) - got) > 1e-6
+
+
 def test_reconstruct_loop_order_and_metric_convention():
     # Step l: z-update with the current probe, object from z^(l), probe from
     # (psi^(l), z^(l)) on probe steps; metrics describe the entering iterate.
