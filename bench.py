@@ -1,20 +1,23 @@
-"""Benchmark: RAAR frame-iterations/s on one GB300 for the 2500-frame 128^2
-Fermat-spiral scan over a 1024^2 object (probe refinement every 2nd step,
-eps_a every step, eps_Q and eps_Delta every 10th), with the fused frame kernel's HBM roofline fraction,
-an end-to-end figure through the C ABI with host buffers, and the FP64 oracle
-timed on the host cores as a reported CPU baseline.
+"""Benchmark: RAAR frame-iterations/s on one GB300 for the 10^4-frame raster
+of 256^2 frames over a 3072^2 object (step 24 +-1 px, Poisson 10^8 photons
+per frame, fixed probe, eps_a every step, eps_Q and eps_Delta every 10th),
+with the fused frame kernel's HBM roofline fraction, an end-to-end figure
+through the C ABI with host buffers, and the FP64 oracle timed on the host
+cores as a reported CPU baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload fermat|raster256|batch|batch-small] [--no-mixed]
-                  [--copy-streams S]
+                  [--workload raster256|fermat|batch|batch-small] [--no-mixed]
+                  [--no-extra] [--copy-streams S]
 
---workload raster256 times the large scan instead: a 100 x 100 raster of
-256^2 frames (step 24 +-1 px) over a 3072^2 object, Poisson 10^8 photons,
-fixed probe.
+The timed region runs the K steps with no timing hooks; a second pass of the
+same steps with the library's per-launch CUDA events gives the per-kernel
+breakdown and the frame kernel's average duration for the roofline.
 
-For 128^2 workloads the line also carries "mixed": the same steps with the
-frame DFTs as FP16 (per-frame scaled) and BF16x3 tensor-core contractions,
-each with its frame-kernel time, HBM fraction and tensor rate.
+Unless --no-extra is given, the line also carries "fermat": the 2500-frame
+128^2 Fermat-spiral scan over a 1024^2 object (probe refinement every 2nd
+step) measured the same way, with "mixed": its steps with the frame DFTs as
+FP16 (per-frame scaled) and BF16x3 tensor-core contractions (128^2 frames).
+--workload fermat makes that scan the headline instead.
 
 Prints one JSON line on rank 0.  Under torchrun (N > 1) every rank runs an
 independent replica of the scan (the path has no exchange step on one box),
@@ -40,8 +43,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RAAR frame-iterations/s on 1 GB300 (FP32 vs mixed) and % of HBM roofline"
 UNIT = "frame-iterations/s"
-WORKLOAD = "fermat-2500x128-obj1024"
 RESIDUAL_EVERY = 10   # eps_Q and eps_Delta every 10th step; eps_a every step
+FRAME_KERNEL = {"fermat": "raar_kernel<128>", "raster256": "big_kernel<RAAR> (256^2 line passes)"}
 PROFILES = {"fermat": os.path.join(ROOT, "profiles", "raar_kernel_fermat128.txt"),
             "raster256": os.path.join(ROOT, "profiles", "big_kernel_raster256.txt")}
 CSRC = os.path.join(ROOT, "paper_1602_01448_gb300", "csrc")
@@ -192,75 +195,76 @@ def device_poisson(amp, photons: float, seed: int):
     return out
 
 
-def oracle_sample_rate(scan, amps, n_frames: int, n_steps: int = 1):
+def oracle_cores() -> int:
+    """Host threads the oracle's transforms use (scipy.fft workers)."""
+    import oracle as O
+    return O.fft_workers()
+
+
+def oracle_step_rate(scan, amps, n_frames: int, n_steps: int = 1):
     """FP64 oracle RAAR steps over the first n_frames frames of the scan (full
-    object): frame-iterations per second of host time."""
+    object), with the probe update on the scan's cadence, as the GPU steps
+    run them (Sec. 2.2 sequence): frame-iterations per second of host time."""
     import oracle as O
     pos = scan.pos[:n_frames]
     a = amps[:n_frames]
-    z = O.split(scan.psi_init, scan.probe_init, pos)
     t0 = time.perf_counter()
-    for _ in range(n_steps):
-        z = O.raar_update(z, a, scan.probe_init, pos, scan.shape, 0.75)
-        O.object_update(z, scan.probe_init, pos, scan.shape)
+    O.raar_reconstruct(a, pos, scan.shape, scan.probe_init, scan.psi_init, n_steps, beta=0.75,
+                       probe_every=scan.probe_every, record_metrics=False)
     dt = time.perf_counter() - t0
     return n_frames * n_steps / dt, dt
 
 
-def host_amplitudes(scan, seed=5):
-    """Noisy amplitudes for the oracle arms, computed with the oracle's forward
-    model (the GPU arm computes its own with the library)."""
+def oracle_amplitudes(scan, n_frames: int, seed: int = 5):
+    """Noisy amplitudes of the first n_frames frames for the oracle arms,
+    computed with the oracle's own forward model (the GPU arm computes its own
+    with the library)."""
     import oracle as O
     import synth
-    inten = O.forward_amplitudes(scan.obj, scan.probe, scan.pos) ** 2
+    inten = O.forward_amplitudes(scan.obj, scan.probe, scan.pos[:n_frames]) ** 2
     return np.sqrt(synth.poisson_intensities(inten, scan.photons, seed))
 
 
 def run_reference(args, rank):
+    """The oracle as the reference arm: every step is one FP64 RAAR step (with
+    the probe update on the scan's cadence) over a sample of the workload's
+    frames, sized so that the K + W steps take about two minutes."""
     if rank != 0:
         return
-    scan = make_scan()
-    n = 500
-    import oracle as O
-    import synth
-    inten = O.forward_amplitudes(scan.obj, scan.probe, scan.pos[:n]) ** 2
-    a = np.sqrt(synth.poisson_intensities(inten, scan.photons, 5))
+    scan = make_scan(None, args.workload)
+    per_frame_s = {64: 0.004, 128: 0.015, 256: 0.06}[scan.m]    # rough single-step cost per frame
+    n = int(max(16, min(500, 120.0 / (per_frame_s * max(1, args.steps + args.warmup)))))
+    n = min(n, scan.K)
+    a = oracle_amplitudes(scan, n)
+    steps_each = 2 if scan.probe_every else 1                    # one step with a probe update
     for _ in range(args.warmup):
-        oracle_sample_rate(scan, a, n)
+        oracle_step_rate(scan, a, n, steps_each)
     times = []
     for _ in range(args.steps):
-        _, dt = oracle_sample_rate(scan, a, n)
-        times.append(dt)
+        _, dt = oracle_step_rate(scan, a, n, steps_each)
+        times.append(dt / steps_each)
     ms = 1000.0 * float(np.mean(times))
     val = n / (ms / 1000.0)
-    sample = f"first {n} of 2500 frames per step, full 1024^2 object, FP64 NumPy"
+    cores = oracle_cores()
+    sample = (f"first {n} of {scan.K} frames of {scan.m}^2 per step, full {scan.shape[0]}^2 object, FP64 "
+              f"NumPy/SciPy, transforms on {cores} threads"
+              + (", probe update every 2nd step" if scan.probe_every else ""))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": sample},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": scan.name, "sample": sample},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-def time_mixed(S, scan, amp, psi0, w0, prec, steps, warmup, world, dev):
-    """The same RAAR steps with the frame DFTs as tensor-core contractions
-    (precision `prec`, 128^2 frames): throughput, frame-kernel time, its HBM
-    fraction (20 m^2 B per frame) and its tensor-pipe rate (4 complex
-    128 x 128 x 128 products per frame = 16 real ones, 2 m^3 flops each; the
-    BF16 three-term split issues each real product three times)."""
+def timed_steps(plan, amp, steps, world, dev):
+    """K RAAR steps between CUDA events on the launching stream, no timing
+    hooks: the max over ranks of the elapsed milliseconds."""
     import torch
-    K, m = scan.K, scan.m
-    plan = S.Plan(scan.pos, m, scan.shape, beta=0.75, probe_every=scan.probe_every,
-                  residual_every=RESIDUAL_EVERY, device=dev, precision=prec)
-    plan.raar_init(psi0, w0)
-    for _ in range(warmup):
-        plan.raar_step(amp)
-    torch.cuda.synchronize()
-    S.sharp_plan_set_profiling(plan.handle, True)
-    S.sharp_plan_kernel_times(plan.handle)
     stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -268,13 +272,57 @@ def time_mixed(S, scan, amp, psi0, w0, prec, steps, warmup, world, dev):
         plan.raar_step(amp)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_total = slowest_rank_ms(e0.elapsed_time(e1), world, dev)
+    return slowest_rank_ms(e0.elapsed_time(e1), world, dev)
+
+
+def kernel_breakdown(S, plan, amp, steps):
+    """The same steps again with the library's per-launch CUDA events on the
+    launching stream: per kernel class (total ms over the steps, launches),
+    and the whole pass's milliseconds with the hooks on."""
+    import torch
+    S.sharp_plan_set_profiling(plan.handle, True)
+    S.sharp_plan_kernel_times(plan.handle)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        plan.raar_step(amp)
+    torch.cuda.synchronize()
+    wall = 1000.0 * (time.perf_counter() - t0)
     kt = S.sharp_plan_kernel_times(plan.handle)
     S.sharp_plan_set_profiling(plan.handle, False)
-    plan.status()
+    return kt, wall
+
+
+def frame_roofline(kt, m, K, peak):
+    """HBM roofline of the fused frame kernel: 20 m^2 B per frame-iteration
+    (state read 8, amplitudes read 4, state write 8) over its average launch
+    duration."""
     frame_ms, frame_n = kt["frame"]
     t_frame = frame_ms / max(frame_n, 1) / 1000.0
+    alg = 20.0 * m * m * K
+    return alg, t_frame, alg / t_frame / 1e9
+
+
+def time_mixed(S, scan, amp, psi0, w0, prec, steps, warmup, world, dev):
+    """The same RAAR steps with the frame DFTs as tensor-core contractions
+    (precision `prec`, 128^2 frames): throughput (hook-free timed steps),
+    frame-kernel time (a second, profiled pass), its HBM fraction (20 m^2 B
+    per frame) and its tensor-pipe rate.  The rate counts the dense-equivalent
+    products issued: 4 complex m x m x m products per frame = 16 real ones,
+    2 m^3 flops each, three times for the BF16 three-term split; the FFT path
+    does ~2.3 MFLOP of useful work per frame against these 67 MFLOP, so the
+    HBM fraction, not the tensor rate, is the figure of merit."""
+    K, m = scan.K, scan.m
+    plan = S.Plan(scan.pos, m, scan.shape, beta=0.75, probe_every=scan.probe_every,
+                  residual_every=RESIDUAL_EVERY, device=dev, precision=prec)
+    plan.raar_init(psi0, w0)
+    for _ in range(warmup):
+        plan.raar_step(amp)
+    ms_total = timed_steps(plan, amp, steps, world, dev)
+    kt, _ = kernel_breakdown(S, plan, amp, steps)
+    plan.status()
     peak_hbm, _ = measured_peak_hbm()
+    alg, t_frame, achieved = frame_roofline(kt, m, K, peak_hbm)
     terms = 3 if prec == "bf16x3" else 1
     flops = 16 * 2.0 * m ** 3 * terms * K
     peak_tc = measured_peak_tensor()
@@ -282,37 +330,38 @@ def time_mixed(S, scan, amp, psi0, w0, prec, steps, warmup, world, dev):
     launches = sum(n for _, n in kt.values())
     out = {"precision": prec, "value": job_throughput(K, steps, world, ms_total), "unit": UNIT,
            "ms_per_step": ms_total / steps, "frame_kernel_ms": t_frame * 1000.0,
-           "hbm": {"achieved": 20.0 * m * m * K / t_frame / 1e9, "peak": peak_hbm, "unit": "GB/s",
-                   "frac": 20.0 * m * m * K / t_frame / 1e9 / peak_hbm},
+           "hbm": {"achieved": achieved, "peak": peak_hbm, "unit": "GB/s", "frac": achieved / peak_hbm},
            "tensor": {"achieved": flops / t_frame / 1e12, "peak": peak_tc, "unit": "TFLOP/s",
                       "frac": flops / t_frame / 1e12 / peak_tc if peak_tc else None,
-                      "flops_per_launch": flops, "terms": terms},
+                      "flops_per_launch": flops, "terms": terms,
+                      "counts": "dense-equivalent products issued, not useful FFT work"},
            "gpu_launches": launches, "last_metrics": {"eps_a": met[0], "eps_q": met[1]}}
     plan.close()
     return out
 
 
-def run_ours(args, rank, world):
+def measure_scan(S, args, workload, frames, world, dev, local, rank, with_e2e=True, with_mixed=True,
+                 with_cpu=True, steps=None):
+    """One workload: hook-free timed steps (value), the per-kernel breakdown
+    and roofline from a profiled pass, e2e with host buffers, the tensor-core
+    modes (128^2) and the oracle on the host cores."""
     import torch
-    import paper_1602_01448_gb300 as S
     import synth
-
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    scan = make_scan(args.frames, args.workload)
+    steps = args.steps if steps is None else steps
+    scan = make_scan(frames, workload)
     K, m = scan.K, scan.m
     plan = S.Plan(scan.pos, m, scan.shape, beta=0.75, probe_every=scan.probe_every, residual_every=RESIDUAL_EVERY,
                   device=dev)
     obj = torch.as_tensor(scan.obj).to(torch.complex64).to(dev)
     probe_true = torch.as_tensor(scan.probe).to(torch.complex64).to(dev)
     amp = plan.forward_amplitudes(obj, probe_true)
-    if args.workload == "fermat":
+    if workload == "fermat":
         inten = (amp.double() ** 2).cpu().numpy()
         amp_h = np.sqrt(synth.poisson_intensities(inten, scan.photons, 5)).astype(np.float32)
         amp = torch.as_tensor(amp_h).to(dev)
     else:
         amp = device_poisson(amp, scan.photons, 5)
+    del obj, probe_true
     psi0 = torch.as_tensor(scan.psi_init).to(torch.complex64).to(dev)
     w0 = torch.as_tensor(scan.probe_init).to(torch.complex64).to(dev)
     plan.raar_init(psi0, w0)
@@ -324,46 +373,82 @@ def run_ours(args, rank, world):
     for _ in range(args.warmup):
         plan.raar_step(amp)
     torch.cuda.synchronize()
-    S.sharp_plan_set_profiling(plan.handle, True)
-    S.sharp_plan_kernel_times(plan.handle)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
     barrier()
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        plan.raar_step(amp)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms_total = timed_steps(plan, amp, steps, world, dev)
     barrier()
     clocks = sampler.stop()
-    ms_total = e0.elapsed_time(e1)
-    kt = S.sharp_plan_kernel_times(plan.handle)
-    S.sharp_plan_set_profiling(plan.handle, False)
     metrics = plan.metrics.cpu().numpy().tolist()
-    ms_total = slowest_rank_ms(ms_total, world, dev)
-    ms_step = ms_total / args.steps
-    value = job_throughput(K, args.steps, world, ms_total)
+    ms_step = ms_total / steps
+    value = job_throughput(K, steps, world, ms_total)
+    plan.status()
 
-    # roofline of the fused frame kernel: 20 m^2 B per frame-iteration
-    frame_ms, frame_n = kt["frame"]
-    t_frame = frame_ms / max(frame_n, 1) / 1000.0
-    alg_bytes = 20.0 * m * m * K
-    achieved = alg_bytes / t_frame / 1e9
+    # per-kernel breakdown and the frame kernel's launch duration (profiled pass)
+    kt, prof_ms = kernel_breakdown(S, plan, amp, steps)
     peak, peak_kind = measured_peak_hbm()
-    launches = sum(n for _, n in kt.values())
+    alg_bytes, t_frame, achieved = frame_roofline(kt, m, K, peak)
+    launches_per_step = sum(n for _, n in kt.values()) / steps
 
-    # end to end through the C ABI with host buffers: every step uploads its
-    # measured amplitudes from pinned host memory and reads the object back.
-    # The upload for step k+1 runs on its own stream while step k computes
-    # (two device buffers), and the object of step k is read back on a third
-    # stream from a device snapshot; every copy of the timed steps lies
-    # inside the timed region (the first upload starts after the start event,
-    # the end event waits for the last read-back).
+    e2e = None
+    if with_e2e:
+        e2e = measure_e2e(plan, amp, args, world, dev, K)
+
+    mixed = []
+    if m == 128 and with_mixed and not args.no_mixed:
+        for prec in ("fp16s", "bf16x3"):
+            mixed.append(time_mixed(S, scan, amp, psi0, w0, prec, steps, args.warmup, world, dev))
+    plan.close()
+    del amp
+    torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and world == 1 and with_cpu and not args.no_cpu_baseline:
+        # a bounded sample of the same steps: 500 frames of 256^2 (the
+        # precision-study subset), all frames of smaller scans; two steps
+        # (one with a probe update) when the scan refines its probe
+        n = 500 if m == 256 else K
+        n_steps = 2 if scan.probe_every else 1
+        a_o = oracle_amplitudes(scan, n)
+        rate, dt = oracle_step_rate(scan, a_o, n, n_steps)
+        cores = oracle_cores()
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n_steps} FP64 RAAR step(s) (object update"
+                         + (", probe update on the 2nd" if scan.probe_every else "")
+                         + f") over {n} of {K} frames (full {scan.shape[0]}^2 object), {dt:.1f} s; "
+                         f"transforms on {cores} threads (scipy.fft), the rest of the oracle single-threaded"}
+    return {
+        "scan": scan, "value": value, "ms_per_step": ms_step, "steps": steps, "clocks": clocks,
+        "config": {"workload": scan.name, "frames": K, "frame": m, "object": list(scan.shape),
+                   "beta": 0.75, "probe_every": scan.probe_every, "residual_every": RESIDUAL_EVERY,
+                   "photons_per_frame": scan.photons, "parallelism": f"replicas{world}",
+                   "l2": f"inputs larger than L2 (c {8 * K * m * m / 1e6:.0f} MB + a {4 * K * m * m / 1e6:.0f} MB per step)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak,
+                     "traffic": profiled_traffic(workload) if frames is None else None,
+                     "kernel": FRAME_KERNEL[workload], "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes, "kernel_ms": t_frame * 1000.0,
+                     "timing": "frame-kernel launches bracketed by CUDA events on the launching stream "
+                               "(profiled pass of the same steps)"},
+        "kernel_ms_per_step": {k: v[0] / steps for k, v in kt.items()},
+        "profiled_pass_ms_per_step": prof_ms / steps,
+        "gpu_launches": int(round(launches_per_step * steps)),
+        "e2e": e2e, "mixed": mixed, "cpu_baseline": cpu,
+        "last_metrics": {"eps_a": metrics[0], "eps_q": metrics[1]},
+    }
+
+
+def measure_e2e(plan, amp, args, world, dev, K):
+    """End to end through the C ABI with host buffers: every step uploads its
+    measured amplitudes from pinned host memory and reads the object back.
+    The upload for step k+1 runs on its own stream while step k computes (two
+    device buffers), and the object of step k is read back on a third stream
+    from a device snapshot; every copy of the timed steps lies inside the
+    timed region (the first upload starts after the start event, the end
+    event waits for the last read-back)."""
+    import torch
+    stream = torch.cuda.current_stream()
     e2e_steps = max(4, min(args.steps, 10))
     amp_pin = torch.empty(amp.shape, dtype=amp.dtype, pin_memory=True)
     amp_pin.copy_(amp)
@@ -418,52 +503,48 @@ def run_ours(args, rank, world):
     stream.wait_event(read[(e2e_steps - 2) % 2])
     f1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1) / e2e_steps
-    e2e_ms = slowest_rank_ms(e2e_ms, world, dev)
+    e2e_ms = slowest_rank_ms(f0.elapsed_time(f1) / e2e_steps, world, dev)
+    out = {"value": world * K / (e2e_ms / 1000.0), "unit": UNIT,
+           "h2d_bytes_per_step": int(amp.numel() * 4), "d2h_bytes_per_step": int(plan.psi.numel() * 8),
+           "ms_per_step": e2e_ms, "copy_streams": n_up, "steps": e2e_steps}
+    del amp_pin, amp_dev, psi_snap, psi_pin
+    return out
 
-    mixed = []
-    if m == 128 and not args.no_mixed:
-        for prec in ("fp16s", "bf16x3"):
-            mixed.append(time_mixed(S, scan, amp, psi0, w0, prec, args.steps, args.warmup, world, dev))
 
+def run_ours(args, rank, world):
+    import torch
+    import paper_1602_01448_gb300 as S
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    head = measure_scan(S, args, args.workload, args.frames, world, dev, local, rank)
+    extra = None
+    if args.workload == "raster256" and not args.no_extra and args.frames is None:
+        # the 128^2 Fermat scan (probe refinement) and its tensor-core modes
+        extra = measure_scan(S, args, "fermat", None, world, dev, local, rank, with_e2e=False, with_cpu=False,
+                             steps=max(args.steps, 50))
     if rank != 0:
         return
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        n = K if m <= 128 else 300
-        import oracle as O
-        inten = O.forward_amplitudes(scan.obj, scan.probe, scan.pos[:n]) ** 2
-        a_o = np.sqrt(synth.poisson_intensities(inten, scan.photons, 5))
-        rate, dt = oracle_sample_rate(scan, a_o, n, 1)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one FP64 RAAR step + object update over {n} of {K} frames "
-                         f"(full {scan.shape[0]}^2 object), {dt:.1f} s, NumPy single thread"}
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": scan.name, "frames": K, "frame": m, "object": list(scan.shape),
-                   "beta": 0.75, "probe_every": scan.probe_every, "residual_every": RESIDUAL_EVERY,
-                   "photons_per_frame": scan.photons, "parallelism": f"replicas{world}",
-                   "l2": f"inputs larger than L2 (c {8 * K * m * m / 1e6:.0f} MB + a {4 * K * m * m / 1e6:.0f} MB per step)"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak,
-                     "traffic": profiled_traffic(args.workload) if args.frames is None else None,
-                     "kernel": "raar_kernel<128>" if m <= 128 else "big_kernel<RAAR> (256^2 line passes)",
-                     "peak_kind": peak_kind,
-                     "alg_bytes_per_launch": alg_bytes, "kernel_ms": t_frame * 1000.0},
-        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
-        "cpu_baseline": cpu,
-        "e2e": {"value": world * K / (e2e_ms / 1000.0), "unit": UNIT,
-                "h2d_bytes_per_step": int(amp.numel() * 4), "d2h_bytes_per_step": int(plan.psi.numel() * 8),
-                "ms_per_step": e2e_ms, "copy_streams": n_up},
-        "gpu_launches": launches,
-        "clocks": clocks,
-        "last_metrics": {"eps_a": metrics[0], "eps_q": metrics[1]},
+        "config": head["config"], "roofline": head["roofline"],
+        "kernel_ms_per_step": head["kernel_ms_per_step"],
+        "profiled_pass_ms_per_step": head["profiled_pass_ms_per_step"],
+        "cpu_baseline": head["cpu_baseline"], "e2e": head["e2e"],
+        "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
+        "last_metrics": head["last_metrics"],
         # the same workload with the frame DFTs as tensor-core contractions
-        # (FP16 per-frame scaled; BF16 three-term), timed after the FP32 run
-        "mixed": mixed,
+        # (FP16 per-frame scaled; BF16 three-term), 128^2 frames only
+        "mixed": head["mixed"],
     }
+    if extra is not None:
+        out["fermat"] = {k: extra[k] for k in ("value", "ms_per_step", "steps", "config", "roofline",
+                                               "kernel_ms_per_step", "gpu_launches", "clocks", "mixed",
+                                               "last_metrics")}
+        out["fermat"]["unit"] = UNIT
     print(json.dumps(out), flush=True)
 
 
@@ -548,16 +629,14 @@ def run_batch(args, rank, world):
     grids = {m: batch.tuned_grid(m) for m in (64, 128, 256)}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        import oracle as O
-        import synth
         sc = scans[0]
         n = min(sc.K, 300)
-        inten = O.forward_amplitudes(sc.obj, sc.probe, sc.pos[:n]) ** 2
-        a_o = np.sqrt(synth.poisson_intensities(inten, sc.photons, 5))
-        rate, dt = oracle_sample_rate(sc, a_o, n, 1)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+        a_o = oracle_amplitudes(sc, n)
+        rate, dt = oracle_step_rate(sc, a_o, n, 1)
+        cores = oracle_cores()
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"one FP64 RAAR step + object update over {n} frames of {sc.m}^2 "
-                         f"(first scan of the batch), {dt:.1f} s, NumPy single thread"}
+                         f"(first scan of the batch), {dt:.1f} s; transforms on {cores} threads (scipy.fft)"}
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (ms_step / 1000.0) / 1e9
     out = {
@@ -588,14 +667,16 @@ def run_batch(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the tensor-core precision modes (128^2 frames)")
     ap.add_argument("--copy-streams", type=int, default=1,
                     help="copy streams sharing each step's host-to-device upload in the e2e measurement")
-    ap.add_argument("--workload", default="fermat", choices=["fermat", "raster256", "batch", "batch-small"])
+    ap.add_argument("--workload", default="raster256", choices=["raster256", "fermat", "batch", "batch-small"])
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the 128^2 Fermat scan (and its tensor-core modes) after the headline workload")
     ap.add_argument("--frames", type=int, default=None,
                     help="frames of the scan (default: the workload's; fewer for small ncu captures; "
                          "raster256 rounds to a square raster)")

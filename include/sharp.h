@@ -286,9 +286,8 @@ int sharp_batch_destroy(sharp_batch batch);
 /*
  * Data projection without device allocation.  The paper has no counterpart:
  * this entry point serves callers that must not allocate device memory while
- * they run -- hosts that own every device allocation, real-time loops that
- * cannot risk the synchronisation an allocation may cause, or work recorded
- * into a CUDA graph.  It needs no plan.
+ * they run -- hosts that own every device allocation, or real-time loops that
+ * cannot risk the synchronisation an allocation may cause.  It needs no plan.
  *   z, out   : float2[K][m][m] (out == z allowed);  amp : float[K][m][m];
  *   resid_sq : DEVICE double[1] or NULL; receives ||P_a z - z||^2, summed over
  *              frames in frame order.

@@ -2,9 +2,8 @@
 //
 // Some callers cannot allocate device memory while they run: a host
 // application that hands this library a fixed memory budget and owns every
-// allocation itself, a real-time loop that must never stall on the allocator
-// (cudaMalloc and cudaFree can synchronise the device), or code that records
-// its work into a CUDA graph, where allocation calls are not allowed.  Such a
+// allocation itself, or a real-time loop that must never stall on the
+// allocator (cudaMalloc and cudaFree can synchronise the device).  Such a
 // caller provides the frames, amplitudes and outputs and calls this entry
 // point, which keeps its only scratch -- one partial residual per frame -- in
 // a fixed array in device global memory that belongs to the library.

@@ -1,15 +1,18 @@
 """The allocation-free data projection (sharp_fourier_project_noalloc) gives
-the same frames and residual as the plan-based sharp_fourier_project.
+the same frames and residual as the plan-based sharp_fourier_project and as
+the FP64 oracle's P_a (Eq. 7), and allocates no device memory.
 
 It exists for callers that cannot allocate device memory while they run, for
-example hosts that own every device allocation or work recorded into a CUDA
-graph; its scratch is a fixed library-owned device array.  This file is named
-so that pytest collects it last; it also passes when run on its own.
+example hosts that own every device allocation or real-time loops that must
+not wait on the allocator; its scratch is a fixed library-owned device array.
+This file is named so that pytest collects it last; it also passes when run
+on its own.
 """
 import numpy as np
 import pytest
 import torch
 
+import oracle as O
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -48,6 +51,34 @@ def test_noalloc_projection_matches_plan_projection_twice(m):
         torch.cuda.synchronize()
         assert _rel(out, ref) < TOL, call
         assert abs(r.item() - r_ref.item()) < TOL * r_ref.item(), call
+        # and directly against the oracle's P_a and ||P_a z - z||^2
+        z_h = z.cpu().numpy().astype(np.complex128)
+        a_h = amp.cpu().numpy().astype(np.float64)
+        p_o = O.data_project(z_h, a_h)
+        got = out.cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(got - p_o) < TOL * np.linalg.norm(p_o), call
+        r_o = O.norm(p_o - z_h) ** 2
+        assert abs(r.item() - r_o) < TOL * r_o, call
+
+
+@pytest.mark.parametrize("m", [64, 128])
+def test_noalloc_call_leaves_device_memory_unchanged(m):
+    import paper_1602_01448_gb300 as S
+    K = 19
+    z = torch.as_tensor(synth.random_frames(K, m, 7)).to(torch.complex64).cuda()
+    amp = torch.as_tensor(synth.random_amplitudes(K, m, 8)).to(torch.float32).cuda()
+    out = torch.empty_like(z)
+    r = torch.zeros(1, dtype=torch.float64, device="cuda")
+    S.sharp_fourier_project_noalloc(z, amp, out, r)      # first call: module load, symbol lookup
+    torch.cuda.synchronize()
+    first = out.clone()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        S.sharp_fourier_project_noalloc(z, amp, out, r)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert _rel(out, first) < TOL
 
 
 def test_noalloc_rejects_too_many_frames():
