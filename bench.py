@@ -305,13 +305,15 @@ def frame_roofline(kt, m, K, peak):
 
 def time_mixed(S, scan, amp, psi0, w0, prec, steps, warmup, world, dev):
     """The same RAAR steps with the frame DFTs as tensor-core contractions
-    (precision `prec`, 128^2 frames): throughput (hook-free timed steps),
-    frame-kernel time (a second, profiled pass), its HBM fraction (20 m^2 B
-    per frame) and its tensor-pipe rate.  The rate counts the dense-equivalent
-    products issued: 4 complex m x m x m products per frame = 16 real ones,
-    2 m^3 flops each, three times for the BF16 three-term split; the FFT path
-    does ~2.3 MFLOP of useful work per frame against these 67 MFLOP, so the
-    HBM fraction, not the tensor rate, is the figure of merit."""
+    (precision `prec`): throughput (hook-free timed steps), frame-kernel time
+    (a second, profiled pass), its HBM fraction (20 m^2 B per frame) and its
+    tensor-pipe rate.  The rate counts the dense-equivalent products issued:
+    4 complex 128 x 128 x 128 products per 128^2 transform pair = 16 real
+    ones, 2 * 128^3 flops each, four such pairs per 256^2 frame (its radix-2
+    split into 128^2 sub-problems), three times for the BF16 three-term split;
+    an FFT does ~2.3 MFLOP (128^2) of useful work per frame against these
+    67 MFLOP, so the HBM fraction, not the tensor rate, is the figure of
+    merit."""
     K, m = scan.K, scan.m
     plan = S.Plan(scan.pos, m, scan.shape, beta=0.75, probe_every=scan.probe_every,
                   residual_every=RESIDUAL_EVERY, device=dev, precision=prec)
@@ -324,7 +326,7 @@ def time_mixed(S, scan, amp, psi0, w0, prec, steps, warmup, world, dev):
     peak_hbm, _ = measured_peak_hbm()
     alg, t_frame, achieved = frame_roofline(kt, m, K, peak_hbm)
     terms = 3 if prec == "bf16x3" else 1
-    flops = 16 * 2.0 * m ** 3 * terms * K
+    flops = 16 * 2.0 * 128 ** 3 * (m // 128) ** 2 * terms * K
     peak_tc = measured_peak_tensor()
     met = plan.metrics.cpu().numpy().tolist()
     launches = sum(n for _, n in kt.values())
@@ -396,7 +398,7 @@ def measure_scan(S, args, workload, frames, world, dev, local, rank, with_e2e=Tr
         e2e = measure_e2e(plan, amp, args, world, dev, K)
 
     mixed = []
-    if m == 128 and with_mixed and not args.no_mixed:
+    if m in (128, 256) and with_mixed and not args.no_mixed:
         for prec in ("fp16s", "bf16x3"):
             mixed.append(time_mixed(S, scan, amp, psi0, w0, prec, steps, args.warmup, world, dev))
     plan.close()
@@ -537,7 +539,7 @@ def run_ours(args, rank, world):
         "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
         "last_metrics": head["last_metrics"],
         # the same workload with the frame DFTs as tensor-core contractions
-        # (FP16 per-frame scaled; BF16 three-term), 128^2 frames only
+        # (FP16 per-frame scaled; BF16 three-term)
         "mixed": head["mixed"],
     }
     if extra is not None:
@@ -546,6 +548,63 @@ def run_ours(args, rank, world):
                                                "last_metrics")}
         out["fermat"]["unit"] = UNIT
     print(json.dumps(out), flush=True)
+
+
+def run_precision_study(args, rank, world):
+    """Errors of the tensor-core precision modes on the 10^4-frame 256^2
+    raster, against the FP64 oracle on a 500-frame subset (the first 5 rows of
+    the raster, full 3072^2 object, Poisson 10^8 photons): the data projection
+    P_a of one set of frames (per operator), and after `steps` RAAR steps from
+    the scan's start the object against the oracle's object and eps_0 (Eq. 14)
+    against the ground truth (final NRMSE).  FP32, BF16x3 and FP16S."""
+    import torch
+    import oracle as O
+    import paper_1602_01448_gb300 as S
+    import synth
+
+    if rank != 0:
+        return
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    full = synth.scan_large_raster()
+    n = 500
+    pos = full.pos[:n]
+    shape, m = full.shape, full.m
+    a = oracle_amplitudes(full, n, seed=9)
+    steps = args.steps
+    t0 = time.perf_counter()
+    ref = O.raar_reconstruct(a, pos, shape, full.probe_init, full.psi_init, steps, beta=0.75,
+                             psi_true=full.obj, record_metrics=False)
+    t_oracle = time.perf_counter() - t0
+    rng = np.random.default_rng(11)
+    z = O.split(full.obj * np.exp(0.3j * rng.standard_normal(shape)), full.probe, pos[:50])
+    pa_ref = O.data_project(z, a[:50])
+    D = O.illumination(full.probe, pos, shape)
+    vis = D > 1e-3 * D.max()
+    out = {}
+    for prec in ("fp32", "bf16x3", "fp16s"):
+        plan = S.Plan(pos, m, shape, beta=0.75, residual_every=0, device=dev, precision=prec)
+        zt = torch.as_tensor(z).to(torch.complex64).to(dev)
+        at = torch.as_tensor(a).to(torch.float32).to(dev)
+        p50 = S.Plan(pos[:50], m, shape, precision=prec, device=dev)
+        got, _ = p50.fourier_project(zt, at[:50].contiguous())
+        pa_err = float(np.linalg.norm(got.cpu().numpy() - pa_ref) / np.linalg.norm(pa_ref))
+        p50.close()
+        plan.raar_init(torch.as_tensor(full.psi_init).to(torch.complex64).to(dev),
+                       torch.as_tensor(full.probe_init).to(torch.complex64).to(dev))
+        for _ in range(steps):
+            plan.raar_step(at, metrics=False)
+        plan.status()
+        e0 = plan.solution_error(plan.psi, torch.as_tensor(full.obj).to(torch.complex64).to(dev),
+                                 torch.as_tensor(full.probe).to(torch.complex64).to(dev))[0].item()
+        psi = plan.psi.cpu().numpy().astype(np.complex128)
+        obj_err = float(np.linalg.norm((psi - ref["psi"])[vis]) / np.linalg.norm(ref["psi"][vis]))
+        out[prec] = {"p_a_rel_l2": pa_err, "object_rel_l2_vs_oracle": obj_err, "eps_0": e0}
+        plan.close()
+    print(json.dumps({"study": "precision", "workload": f"{full.name} subset: first {n} frames",
+                      "steps": steps, "oracle_eps_0": ref["history"][-1]["eps_0"], "oracle_s": t_oracle,
+                      "p_a_frames": 50, "modes": out}), flush=True)
 
 
 def batch_scans(n_scans: int = 32, seed: int = 7, small: bool = False):
@@ -671,10 +730,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the tensor-core precision modes (128^2 frames)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the tensor-core precision modes")
     ap.add_argument("--copy-streams", type=int, default=1,
                     help="copy streams sharing each step's host-to-device upload in the e2e measurement")
-    ap.add_argument("--workload", default="raster256", choices=["raster256", "fermat", "batch", "batch-small"])
+    ap.add_argument("--workload", default="raster256",
+                    choices=["raster256", "fermat", "batch", "batch-small", "precision256"])
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 128^2 Fermat scan (and its tensor-core modes) after the headline workload")
     ap.add_argument("--frames", type=int, default=None,
@@ -692,6 +752,8 @@ def main():
         torch.distributed.init_process_group("nccl")
     if args.workload in ("batch", "batch-small"):
         run_batch(args, rank, world)
+    elif args.workload == "precision256":
+        run_precision_study(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

@@ -49,10 +49,12 @@ extern "C" {
 
 #define SHARP_PREC_FP32            0  /* FP32 data and transforms, FP64 global sums */
 /*
- * Tensor-core precision modes (m = 128 only).  The 2D DFTs of the RAAR frame
- * pass (sharp_raar_step) and of the data projection (sharp_fourier_project)
- * run as contractions with the m x m DFT matrix of Eq. 2 on the tensor cores,
- * FP32 accumulation; data, metrics and every other operator stay FP32 / FP64.
+ * Tensor-core precision modes (m = 128 or 256).  The 2D DFTs of the RAAR
+ * frame pass (sharp_raar_step) and of the data projection
+ * (sharp_fourier_project) run as contractions with the 128 x 128 DFT matrix
+ * of Eq. 2 on the tensor cores, FP32 accumulation (a 256-point transform is
+ * split once, radix 2, into 128-point ones); data, metrics and every other
+ * operator stay FP32 / FP64.
  *   SHARP_PREC_FP16S  : FP16 operands; each operand matrix is scaled per frame
  *                       by a power of two (its largest component mapped into
  *                       [2^14, 2^15)) so that FP16's range is never left.
@@ -72,7 +74,7 @@ typedef struct {
     int   wrap;          /* 1: object indexed modulo its size (periodic boundary, Fig. 3) */
     int   probe_every;   /* refine the probe (Eq. 10) on steps with iter % probe_every == 0; 0 = never */
     int   residual_every;/* eps_Q and eps_Delta (Eqs. 12, 13) on steps with iter % residual_every == 0; 0 = never */
-    int   precision;     /* SHARP_PREC_FP32, or SHARP_PREC_FP16S / SHARP_PREC_BF16X3 (m = 128) */
+    int   precision;     /* SHARP_PREC_FP32, or SHARP_PREC_FP16S / SHARP_PREC_BF16X3 (m = 128, 256) */
 } sharp_params;
 
 /* Message of the last failed call on this thread ("" if none).  Never NULL. */
@@ -96,11 +98,11 @@ void sharp_default_params(sharp_params* p);
  * per-tile frame lists, reduction buffers; for m = 256 also one m x m
  * transposition slab per SM, 78 MB on 152 SMs).  The per-block lists of frames
  * that touch each image block (Sec. 2.3) are built here once, on the host.
- * With a tensor-core precision mode the plan also holds the DFT matrix parts
- * (64 KB for FP16S, 128 KB for BF16X3).
+ * With a tensor-core precision mode the plan also holds the 128 x 128 DFT
+ * matrix parts (64 KB for FP16S, 128 KB for BF16X3).
  * Errors: INVALID_ARG (K < 1, ny or nx < m, bad position, beta outside
  * (0.5, 1], unknown precision), UNSUPPORTED_SIZE (m without a kernel, or a
- * tensor-core mode with m != 128).
+ * tensor-core mode with m = 64).
  */
 int sharp_plan_create(sharp_plan* plan, int K, int m, int ny, int nx,
                       const int32_t* pos, const sharp_params* params,
@@ -256,16 +258,23 @@ int sharp_amp_loss_backward(sharp_plan plan, const float2* obj, const float2* pr
  * per frame size over the frames of all scans of that size, then each scan's
  * image pass, metrics and probe update.  The launch sequence of each distinct
  * step schedule is recorded as a CUDA graph on first use and replayed
- * afterwards; while the grid autotuner is still trying blocks-per-SM
- * candidates (the first steps of a frame size with several), steps run
- * without graphs and synchronise the stream.  Results do not depend on the
- * grid or on graphs.
+ * afterwards.  The launch shape of each frame size is chosen by an autotuner
+ * on the first steps: blocks per SM, rows per round trip of the frame pass's
+ * gathers and scatter (4, 8, 16; 4, 8 for 256^2 frames) and the block-start
+ * stagger, one parameter at a time, each candidate timed once; while it runs,
+ * steps go without graphs and synchronise the stream.  The choice is kept for
+ * the process per frame size and batch size class (frames rounded down to a
+ * power of two), so later batches of the class start tuned.  Results do not
+ * depend on the shape or on graphs beyond the order of the atomic sums.
  *   plans : nscans plans, already set up with sharp_raar_init; they must share
  *           probe_every and residual_every and be stepped only through the
  *           batch, and use SHARP_PREC_FP32.  The batch does not own them.
  * sharp_batch_bind gives scan `scan` its state buffers (as sharp_raar_step;
  * probe and metrics may be NULL); rebinding drops the recorded graphs.
- * sharp_batch_tuned_grid returns the grid chosen for frame size m (or -1).
+ * sharp_batch_tuned_grid returns the grid chosen for frame size m (or -1);
+ * sharp_batch_tuned_shape gives the whole shape (STATE while still tuning);
+ * sharp_batch_set_shape fixes it instead (INVALID_ARG outside the
+ * candidates; drops the recorded graphs).
  * sharp_batch_status synchronises `stream` and returns SHARP_ERR_TIMEOUT
  * (once) if a bounded wait of a batched frame pass gave up, or
  * SHARP_ERR_INVALID_ARG if a scan's measured amplitudes hold a value that is
@@ -280,6 +289,8 @@ int sharp_batch_bind(sharp_batch batch, int scan, float2* state_c, float2* psi_y
 int sharp_batch_step(sharp_batch batch, int iter, cudaStream_t stream);
 int sharp_batch_set_graphs(sharp_batch batch, int enable);
 int sharp_batch_tuned_grid(sharp_batch batch, int m);
+int sharp_batch_tuned_shape(sharp_batch batch, int m, int* grid, int* rows, int* stagger_ns);
+int sharp_batch_set_shape(sharp_batch batch, int m, int grid, int rows, int stagger_ns);
 int sharp_batch_status(sharp_batch batch, cudaStream_t stream);
 int sharp_batch_destroy(sharp_batch batch);
 

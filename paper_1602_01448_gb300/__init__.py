@@ -89,6 +89,8 @@ _lib_fns = {
     "sharp_batch_step": ([_P, _I, _P], _I),
     "sharp_batch_set_graphs": ([_P, _I], _I),
     "sharp_batch_tuned_grid": ([_P, _I], _I),
+    "sharp_batch_tuned_shape": ([_P, _I, _P, _P, _P], _I),
+    "sharp_batch_set_shape": ([_P, _I, _I, _I, _I], _I),
     "sharp_batch_status": ([_P, _P], _I),
     "sharp_batch_destroy": ([_P], _I),
     "sharp_plan_kernel_times": ([_P, _P, _P], _I),
@@ -97,7 +99,7 @@ _C = {name: _decl(name, *sig) for name, sig in _lib_fns.items()}
 
 
 # sharp_params.precision: FP32 transforms, or the frame DFTs as tensor-core
-# contractions (m = 128): FP16 with per-frame power-of-two scaling, or BF16
+# contractions (m = 128, 256): FP16 with per-frame power-of-two scaling, or BF16
 # three-term split; FP32 accumulation in both.
 SHARP_PREC_FP32 = 0
 SHARP_PREC_FP16S = 1
@@ -396,6 +398,15 @@ class Batch:
 
     def tuned_grid(self, m):
         return int(_C["sharp_batch_tuned_grid"](self.handle, int(m)))
+
+    def tuned_shape(self, m):
+        """(grid, rows per round trip, stagger ns) chosen for frame size m."""
+        g, r, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_C["sharp_batch_tuned_shape"](self.handle, int(m), ctypes.byref(g), ctypes.byref(r), ctypes.byref(st)))
+        return g.value, r.value, st.value
+
+    def set_shape(self, m, grid, rows, stagger_ns):
+        _check(_C["sharp_batch_set_shape"](self.handle, int(m), int(grid), int(rows), int(stagger_ns)))
 
     def status(self, stream=None):
         _check(_C["sharp_batch_status"](self.handle, _stream(stream)))

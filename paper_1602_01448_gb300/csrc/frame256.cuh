@@ -120,12 +120,14 @@ __device__ __forceinline__ void col_inv(float2 (&v)[16], float2* E, const float2
 }
 
 // ---------------------------------------------------------------- phases
-// Pass 1: form the frame samples of row y at x = 16 n + j.
-template <int MODE, int FLAGS>
+// Pass 1: form the frame samples of row y at x = 16 n + j, loading RCH
+// samples per round trip in the RAAR mode without metrics (a tile parameter
+// of the batch tuner), 4 otherwise.
+template <int MODE, int FLAGS, int RCH = 8>
 __device__ __forceinline__ void form_row(const FrameArgs& a, int py, int px, size_t fo, int y, int j,
                                          float2 (&v)[16], float (&acc)[5], uint64_t pol_stream,
                                          uint64_t pol_keep) {
-    constexpr int CH = 4;
+    constexpr int CH = (MODE == MODE_RAAR && !(FLAGS & RF_METRIC)) ? RCH : 4;
 #pragma unroll
     for (int n0 = 0; n0 < 16; n0 += CH) {
         if constexpr (MODE == MODE_RAAR) {
@@ -230,11 +232,12 @@ __device__ __forceinline__ void fourier_col(const FrameArgs& a, size_t fo, int x
     }
 }
 
-// Pass 3: epilogue of row y, v[n] = result at x = 16 n + j.
-template <int MODE>
+// Pass 3: epilogue of row y, v[n] = result at x = 16 n + j (RCH samples per
+// round trip in the RAAR mode).
+template <int MODE, int RCH = 8>
 __device__ __forceinline__ void finish_row(const FrameArgs& a, int py, int px, size_t fo, int y, int j,
                                            const float2 (&v)[16], uint64_t pol_stream, uint64_t pol_keep) {
-    constexpr int CH = 4;
+    constexpr int CH = MODE == MODE_RAAR ? RCH : 4;
 #pragma unroll
     for (int n0 = 0; n0 < 16; n0 += CH) {
         if constexpr (MODE == MODE_RAAR) {
@@ -276,7 +279,7 @@ __device__ __forceinline__ void finish_row(const FrameArgs& a, int py, int px, s
 // ---------------------------------------------------------------- kernel
 // `ap` serves a single scan when bt.scans is null; otherwise frames come
 // from the scans of `bt`.  `slab` holds gridDim.x frames of scratch.
-template <int MODE, int FLAGS>
+template <int MODE, int FLAGS, int RCH = 8>
 __global__ void __launch_bounds__(NT, 1) big_kernel(const FrameArgs ap, const BatchTable bt, float2* slab) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2* Ebuf = reinterpret_cast<float2*>(smem_raw);
@@ -292,7 +295,7 @@ __global__ void __launch_bounds__(NT, 1) big_kernel(const FrameArgs ap, const Ba
     for (int i = tid; i < TW; i += NT) tw[i] = c_tw256x16[i];
     if (tid == 0) {
         if (!batch) a = ap;
-        __nanosleep(2000u * (blockIdx.x & 3u));
+        __nanosleep((batch ? (unsigned)bt.stagger_ns : 2000u) * (blockIdx.x & 3u));
     }
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(NT, 1) big_kernel(const FrameArgs ap, const Ba
         for (int r0 = 0; r0 < M; r0 += LINES) {
             const int y = r0 + line;
             float2 v[16];
-            form_row<MODE, FLAGS>(a, py, px, fo, y, jr, v, acc, pol_stream, pol_keep);
+            form_row<MODE, FLAGS, RCH>(a, py, px, fo, y, jr, v, acc, pol_stream, pol_keep);
             row_fwd(v, Ebuf + eb * E_ELEMS, tw, line, jr);
             eb ^= 1;
 #pragma unroll
@@ -396,7 +399,7 @@ __global__ void __launch_bounds__(NT, 1) big_kernel(const FrameArgs ap, const Ba
                 for (int q = 0; q < 16; ++q) v[q] = ld_hint(scr + y * M + jr + 16 * q, pol_keep);
                 row_inv(v, Ebuf + eb * E_ELEMS, tw, line, jr);
                 eb ^= 1;
-                finish_row<MODE>(a, py, px, fo, y, jr, v, pol_stream, pol_keep);
+                finish_row<MODE, RCH>(a, py, px, fo, y, jr, v, pol_stream, pol_keep);
             }
         }
 #pragma unroll
@@ -420,9 +423,9 @@ inline cudaError_t big_max_grid(int* grid) {
     return e;
 }
 
-template <int MODE, int FLAGS>
+template <int MODE, int FLAGS, int RCH = 8>
 cudaError_t big_launch(const FrameArgs& a, const BatchTable* bt, int grid, float2* slab, cudaStream_t s) {
-    auto kern = big::big_kernel<MODE, FLAGS>;
+    auto kern = big::big_kernel<MODE, FLAGS, RCH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big::SMEM);
     if (e != cudaSuccess) return e;
     int maxg = 0;

@@ -54,12 +54,13 @@ __device__ __forceinline__ T ldg_plain(const T* p) { return *p; }
 // `a` is the scan's arguments (kernel parameter or a shared-memory copy).
 
 // z = w_f . psi_y(r + x_i) + c_i into v (pass-1 layout); c_i is in S.
-template <int M, int FLAGS, int WRAP>
+// CH rows are loaded per round trip (a tile parameter of the batch tuner).
+template <int M, int FLAGS, int WRAP, int CH = 8>
 __device__ __forceinline__ void raar_load_phase(const FrameArgs& a, int py, int px, size_t fo, const float2* S,
                                                 float2 (&v)[32], float (&acc)[5], uint64_t pol_stream,
                                                 uint64_t pol_keep) {
     constexpr int TX = Fft3<M>::TX;
-    constexpr int CH = 8;
+    static_assert(32 % CH == 0, "row chunks divide the 32 rows of a thread");
     const int q = threadIdx.x / M;
     const int x = threadIdx.x % M;
     // Per chunk of CH rows: issue every load first, then compute, then store
@@ -138,12 +139,12 @@ __device__ __forceinline__ void raar_fourier_phase(const FrameArgs& a, size_t fo
     }
 }
 
-// Store c_new and scatter C' += conj(w_p) (c_new - (1-b) w_p psi) (pass-1 layout).
-template <int M, int WRAP>
+// Store c_new and scatter C' += conj(w_p) (c_new - (1-b) w_p psi) (pass-1
+// layout), CH rows per round trip.
+template <int M, int WRAP, int CH = 8>
 __device__ __forceinline__ void raar_epilogue(const FrameArgs& a, int py, int px, size_t fo, const float2 (&v)[32],
                                               uint64_t pol_stream, uint64_t pol_keep) {
     constexpr int TX = Fft3<M>::TX;
-    constexpr int CH = 8;
     const int q = threadIdx.x / M;
     const int x = threadIdx.x % M;
     const float rho = 1.f - a.beta;
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_kernel(cons
 // are flushed to the scan it leaves.  Scans may differ in everything but the
 // frame size and the step's flags (FORM_B / METRIC are compile-time).
 
-template <int M, int FLAGS>
+template <int M, int FLAGS, int CH>
 __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_batch_kernel(const BatchTable bt) {
     using G = Fft3<M>;
     using R = RaarGeo<M>;
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_batch_kerne
             if (t.read_e) bulk_prefetch_l2(t.ebuf + (size_t)f * MM, (unsigned)(MM * sizeof(float2)));
     };
     if (tid == 0) {
-        __nanosleep(2000u * (blockIdx.x & 3u));
+        __nanosleep((unsigned)bt.stagger_ns * (blockIdx.x & 3u));
         const int g = atomicAdd(bt.counter, 1);
         s_next = g;
         s_next_scan = g < bt.total ? scan_of(g) : 0;
@@ -376,8 +377,8 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_batch_kerne
         c_pending = false;
         const int nxt = s_next, nxt_scan = s_next_scan;
 
-        if (sa.wrap) raar_load_phase<M, FLAGS, 1>(sa, py, px, fo, S, v, acc, pol_stream, pol_keep);
-        else raar_load_phase<M, FLAGS, 0>(sa, py, px, fo, S, v, acc, pol_stream, pol_keep);
+        if (sa.wrap) raar_load_phase<M, FLAGS, 1, CH>(sa, py, px, fo, S, v, acc, pol_stream, pol_keep);
+        else raar_load_phase<M, FLAGS, 0, CH>(sa, py, px, fo, S, v, acc, pol_stream, pol_keep);
         G::forward(v, S, tw);
         raar_fourier_phase<M>(sa, fo, v, acc, bad);
         G::inverse(v, S, tw);
@@ -388,8 +389,8 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_batch_kerne
             if (tid == 0) issue_c(nxt, nxt_scan);
             c_pending = true;
         }
-        if (sa.wrap) raar_epilogue<M, 1>(sa, py, px, fo, v, pol_stream, pol_keep);
-        else raar_epilogue<M, 0>(sa, py, px, fo, v, pol_stream, pol_keep);
+        if (sa.wrap) raar_epilogue<M, 1, CH>(sa, py, px, fo, v, pol_stream, pol_keep);
+        else raar_epilogue<M, 0, CH>(sa, py, px, fo, v, pol_stream, pol_keep);
         cur = nxt;
         cur_scan = nxt_scan;
     }
@@ -405,10 +406,10 @@ __global__ void __launch_bounds__(Fft3<M>::NT, M == 64 ? 3 : 1) raar_batch_kerne
     if (loaded_scan >= 0) flush(loaded_scan);
 }
 
-template <int M, int FLAGS>
+template <int M, int FLAGS, int CH>
 static cudaError_t launch_raar_batch_one(const BatchTable& bt, int grid, cudaStream_t s) {
     using R = RaarGeo<M>;
-    auto kern = raar_batch_kernel<M, FLAGS>;
+    auto kern = raar_batch_kernel<M, FLAGS, CH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(bt.counter, 0, sizeof(int), s)) != cudaSuccess) return e;
@@ -420,7 +421,7 @@ static cudaError_t launch_raar_batch_one(const BatchTable& bt, int grid, cudaStr
 template <int M>
 cudaError_t raar_batch_max_grid(int* grid) {
     using R = RaarGeo<M>;
-    auto kern = raar_batch_kernel<M, 0>;
+    auto kern = raar_batch_kernel<M, 0, 8>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
@@ -432,13 +433,14 @@ cudaError_t raar_batch_max_grid(int* grid) {
     return cudaSuccess;
 }
 
-template <int M>
-cudaError_t launch_raar_batch_m(int flags, const BatchTable& bt, int grid, cudaStream_t s) {
+// All flag variants of one (frame size, row chunk) pair.
+template <int M, int CH>
+cudaError_t launch_raar_batch_mc(int flags, const BatchTable& bt, int grid, cudaStream_t s) {
     switch (flags & (RF_FORM_B | RF_METRIC)) {
-        case 0: return launch_raar_batch_one<M, 0>(bt, grid, s);
-        case RF_FORM_B: return launch_raar_batch_one<M, RF_FORM_B>(bt, grid, s);
-        case RF_METRIC: return launch_raar_batch_one<M, RF_METRIC>(bt, grid, s);
-        default: return launch_raar_batch_one<M, RF_FORM_B | RF_METRIC>(bt, grid, s);
+        case 0: return launch_raar_batch_one<M, 0, CH>(bt, grid, s);
+        case RF_FORM_B: return launch_raar_batch_one<M, RF_FORM_B, CH>(bt, grid, s);
+        case RF_METRIC: return launch_raar_batch_one<M, RF_METRIC, CH>(bt, grid, s);
+        default: return launch_raar_batch_one<M, RF_FORM_B | RF_METRIC, CH>(bt, grid, s);
     }
 }
 

@@ -154,9 +154,14 @@ void sharp::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 
 cudaError_t sharp::launch_mixed(int prec, int mode, int flags, const FrameArgs& a, cudaStream_t s) {
     if (a.K <= 0) return cudaSuccess;
-    if (a.m != 128 || !a.dft_tab) return cudaErrorInvalidValue;
-    if (prec == SHARP_PREC_FP16S) return launch_mixed_prec<SHARP_PREC_FP16S>(mode, flags, a, s);
-    if (prec == SHARP_PREC_BF16X3) return launch_mixed_prec<SHARP_PREC_BF16X3>(mode, flags, a, s);
+    if (!a.dft_tab) return cudaErrorInvalidValue;
+    if (a.m == 128) {
+        if (prec == SHARP_PREC_FP16S) return launch_mixed_prec<SHARP_PREC_FP16S>(mode, flags, a, s);
+        if (prec == SHARP_PREC_BF16X3) return launch_mixed_prec<SHARP_PREC_BF16X3>(mode, flags, a, s);
+    } else if (a.m == 256) {
+        if (prec == SHARP_PREC_FP16S) return launch_mixed256_prec<SHARP_PREC_FP16S>(mode, flags, a, a.scratch, s);
+        if (prec == SHARP_PREC_BF16X3) return launch_mixed256_prec<SHARP_PREC_BF16X3>(mode, flags, a, a.scratch, s);
+    }
     return cudaErrorInvalidValue;
 }
 
@@ -293,8 +298,8 @@ int sharp_plan_create(sharp_plan* out, int K, int m, int ny, int nx, const int32
     if (prm.probe_every < 0 || prm.residual_every < 0) return fail(SHARP_ERR_INVALID_ARG, "negative cadence");
     if (prm.precision != SHARP_PREC_FP32 && prm.precision != SHARP_PREC_FP16S && prm.precision != SHARP_PREC_BF16X3)
         return fail(SHARP_ERR_INVALID_ARG, "unknown precision %d", prm.precision);
-    if (prm.precision != SHARP_PREC_FP32 && m != 128)
-        return fail(SHARP_ERR_UNSUPPORTED_SIZE, "tensor-core precision modes need m = 128 (m = %d)", m);
+    if (prm.precision != SHARP_PREC_FP32 && m != 128 && m != 256)
+        return fail(SHARP_ERR_UNSUPPORTED_SIZE, "tensor-core precision modes need m = 128 or 256 (m = %d)", m);
 
     std::vector<int32_t> hpos((size_t)K * 2);
     SHARP_CK(cudaMemcpyAsync(hpos.data(), pos, hpos.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
@@ -379,7 +384,7 @@ int sharp_plan_create(sharp_plan* out, int K, int m, int ny, int nx, const int32
     }
     std::vector<uint16_t> dft;
     if (prm.precision != SHARP_PREC_FP32) {
-        dft = dft_table(prm.precision, m);
+        dft = dft_table(prm.precision, m == 256 ? 128 : m);   // 256^2 frames: four 128^2 sub-problems
         if (e == cudaSuccess) e = cudaMalloc(&p.dft_tab, dft.size() * sizeof(uint16_t));
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(p.dft_tab, dft.data(), dft.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, stream);

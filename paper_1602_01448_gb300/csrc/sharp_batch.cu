@@ -7,16 +7,27 @@
 // only on the step's schedule (flags, metric cadence, probe update), so it is
 // recorded once per schedule as a CUDA graph and replayed afterwards.
 //
-// The grid of each frame-size group is chosen online: the first steps try
-// each candidate number of resident blocks per SM (the grid only changes how
-// frames are scheduled, never the result), time the frame pass with events,
-// and keep the fastest for the remaining steps.
+// The launch shape of each frame-size group is chosen online by a small
+// autotuner: the number of resident blocks per SM, the rows each thread loads
+// and stores per round trip of the gathers and the scatter (the frame pass's
+// tile shape: 4, 8 or 16 rows for 64^2 and 128^2 frames, 4 or 8 for 256^2),
+// and whether block starts are staggered.  The first steps time one
+// candidate each with events around the group's frame pass, one parameter
+// at a time (coordinate descent: grid, then rows, then stagger, each from the
+// best so far), and keep the fastest.  None of these changes the arithmetic
+// of a frame; only the order of the atomic overlap sums differs.  The choice
+// is kept for the process, per frame size and size class of the batch
+// (frames rounded down to a power of two), so later batches of that class
+// start tuned.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "sharp_common.cuh"
@@ -32,6 +43,12 @@ struct Bind {
     double* metrics = nullptr;
 };
 
+struct Shape {                    // launch shape of a group's frame pass
+    int grid = 0;                 // blocks (a multiple of the SM count)
+    int ch = 8;                   // rows per load / epilogue round trip
+    int stagger = 2000;           // ns between the starts of blocks b % 4 = 0, 1, 2, 3
+};
+
 struct Group {                    // scans of one frame size
     int m = 0;
     std::vector<int> scans;       // indices into the batch
@@ -39,10 +56,75 @@ struct Group {                    // scans of one frame size
     int* d_base = nullptr;
     float2* slab = nullptr;       // 256^2 frames: one frame of scratch per block
     int max_grid = 0;
-    std::vector<int> candidates;  // grid candidates (autotuner)
+    // autotuner: candidates of the current parameter, their times, the best so far
+    int stage = 0;                // 0 grid, 1 rows, 2 stagger, 3 done
+    std::vector<Shape> cand;
     std::vector<float> cand_ms;
-    int best = -1;
+    Shape best;
+    float best_ms = -1.f;
+    bool tuned = false;
 };
+
+// Tuned shapes of this process: (frame size, size class) -> shape.
+std::mutex g_tuned_mutex;
+std::map<std::pair<int, int>, Shape> g_tuned;
+
+int size_class(int frames) {
+    int c = 0;
+    while ((frames >> (c + 1)) > 0) ++c;
+    return c;
+}
+
+// Candidates of the next tuner stage (each differs from g.best in one
+// parameter); false when no stage is left.
+bool next_stage(Group& g, int sms) {
+    g.cand.clear();
+    while (g.cand.empty() && g.stage < 3) {
+        if (g.stage == 0) {
+            for (int k = 1; k * sms <= g.max_grid; ++k) {
+                Shape s = g.best;
+                s.grid = k * sms;
+                g.cand.push_back(s);
+            }
+            if (g.cand.empty()) {
+                Shape s = g.best;
+                s.grid = g.max_grid;
+                g.cand.push_back(s);
+            }
+        } else if (g.stage == 1) {
+            for (int ch : (g.m == 256 ? std::vector<int>{4, 8} : std::vector<int>{4, 8, 16}))
+                if (ch != g.best.ch) {
+                    Shape s = g.best;
+                    s.ch = ch;
+                    g.cand.push_back(s);
+                }
+        } else {
+            Shape s = g.best;
+            s.stagger = g.best.stagger ? 0 : 2000;
+            g.cand.push_back(s);
+        }
+        ++g.stage;
+    }
+    g.cand_ms.assign(g.cand.size(), -1.f);
+    return !g.cand.empty();
+}
+
+// Record the time of candidate k; move on when the stage is complete.
+void tuner_record(Group& g, int k, float ms, int sms) {
+    g.cand_ms[k] = ms;
+    for (float t : g.cand_ms)
+        if (t < 0.f) return;
+    for (size_t j = 0; j < g.cand.size(); ++j)
+        if (g.best_ms < 0.f || g.cand_ms[j] < g.best_ms) {
+            g.best_ms = g.cand_ms[j];
+            g.best = g.cand[j];
+        }
+    if (!next_stage(g, sms)) {
+        g.tuned = true;
+        std::lock_guard<std::mutex> lk(g_tuned_mutex);
+        g_tuned[{g.m, size_class(g.total)}] = g.best;
+    }
+}
 
 struct Schedule {                 // one distinct step schedule
     cudaGraphExec_t exec = nullptr;            // its recorded launches (graphs on, tuning done)
@@ -70,9 +152,8 @@ struct sharp_batch_s {
 
 namespace {
 
-template <int M>
-cudaError_t group_launch(const Group& g, const sharp::FrameArgs* table, int flags, int grid, int* counter, int* err,
-                         cudaStream_t s) {
+cudaError_t launch_group(const Group& g, const sharp::FrameArgs* table, int flags, const Shape& sh, int* counter,
+                         int* err, cudaStream_t s) {
     sharp::BatchTable bt;
     bt.scans = table;
     bt.base = g.d_base;
@@ -80,25 +161,13 @@ cudaError_t group_launch(const Group& g, const sharp::FrameArgs* table, int flag
     bt.total = g.total;
     bt.counter = counter;
     bt.err = err;
-    return sharp::launch_raar_batch_m<M>(flags, bt, grid, s);
-}
-
-cudaError_t launch_group(const Group& g, const sharp::FrameArgs* table, int flags, int grid, int* counter, int* err,
-                         cudaStream_t s) {
+    bt.stagger_ns = sh.stagger;
     if (g.m == 256) {
-        sharp::BatchTable bt;
-        bt.scans = table;
-        bt.base = g.d_base;
-        bt.nscans = (int)g.scans.size();
-        bt.total = g.total;
-        bt.counter = counter;
-        bt.err = err;
         sharp::FrameArgs none;
         memset(&none, 0, sizeof(none));
-        return sharp::launch_big_raar(flags, none, &bt, grid, g.slab, s);
+        return sharp::launch_big_raar(flags, none, &bt, sh.grid, g.slab, s, sh.ch);
     }
-    return g.m == 64 ? group_launch<64>(g, table, flags, grid, counter, err, s)
-                     : group_launch<128>(g, table, flags, grid, counter, err, s);
+    return sharp::launch_raar_batch(g.m, sh.ch, flags, bt, sh.grid, s);
 }
 
 void drop_schedules(sharp_batch b) {
@@ -156,10 +225,16 @@ int sharp_batch_create(sharp_batch* out, int nscans, const sharp_plan* plans) {
             sharp_batch_destroy(b);
             return bfail(SHARP_ERR_CUDA, cudaGetErrorString(e));
         }
-        for (int k = 1; k * sms <= g.max_grid; ++k) g.candidates.push_back(k * sms);
-        if (g.candidates.empty()) g.candidates.push_back(g.max_grid);
-        g.cand_ms.assign(g.candidates.size(), -1.f);
-        if (g.candidates.size() == 1) g.best = 0;
+        g.best.grid = std::min(sms, g.max_grid);
+        {
+            std::lock_guard<std::mutex> lk(g_tuned_mutex);
+            auto it = g_tuned.find({m, size_class(g.total)});
+            if (it != g_tuned.end() && it->second.grid <= g.max_grid) {
+                g.best = it->second;
+                g.tuned = true;
+            }
+        }
+        if (!g.tuned) next_stage(g, sms);
         b->groups.push_back(g);
     }
     cudaError_t e = cudaMalloc(&b->counter, sizeof(int));
@@ -222,7 +297,7 @@ int sharp_batch_step(sharp_batch b, int iter, cudaStream_t stream) {
             if (info[i].flags != gflags[gi]) return bfail(SHARP_ERR_STATE, "scans of a batch reached different schedules");
     }
     bool tuning = false;
-    for (auto& g : b->groups) tuning |= g.best < 0;
+    for (auto& g : b->groups) tuning |= !g.tuned;
     const bool use_graph = b->use_graphs && !tuning;
     // 2. device argument tables of this schedule (made once, outside any capture)
     Schedule& sch = b->schedules[sig];
@@ -264,32 +339,26 @@ int sharp_batch_step(sharp_batch b, int iter, cudaStream_t stream) {
         cudaError_t e = sharp::raar_step_clear(b->plans[i]->p, s);
         if (e != cudaSuccess) rc = bfail(SHARP_ERR_CUDA, cudaGetErrorString(e));
     }
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (size_t gi = 0; gi < b->groups.size() && rc == SHARP_OK; ++gi) {
         Group& g = b->groups[gi];
-        int cand = g.best >= 0 ? g.best : 0;
-        if (g.best < 0) {
+        const bool timing = !use_graph && !g.tuned;
+        int cand = -1;
+        if (timing)
             for (size_t k = 0; k < g.cand_ms.size(); ++k)
                 if (g.cand_ms[k] < 0.f) { cand = (int)k; break; }
-        }
-        const bool timing = !use_graph && g.best < 0;
+        const Shape sh = cand >= 0 ? g.cand[cand] : g.best;
         cudaError_t e = cudaSuccess;
-        if (timing) e = cudaEventRecord(b->ev0, s);
-        if (e == cudaSuccess)
-            e = launch_group(g, sch.tables[gi], gflags[gi], g.candidates[cand], b->counter, b->err, s);
-        if (e == cudaSuccess && timing) e = cudaEventRecord(b->ev1, s);
-        if (e == cudaSuccess && timing) e = cudaEventSynchronize(b->ev1);
-        if (e == cudaSuccess && timing) {
+        if (cand >= 0) e = cudaEventRecord(b->ev0, s);
+        if (e == cudaSuccess) e = launch_group(g, sch.tables[gi], gflags[gi], sh, b->counter, b->err, s);
+        if (e == cudaSuccess && cand >= 0) e = cudaEventRecord(b->ev1, s);
+        if (e == cudaSuccess && cand >= 0) e = cudaEventSynchronize(b->ev1);
+        if (e == cudaSuccess && cand >= 0) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, b->ev0, b->ev1);
-            g.cand_ms[cand] = ms;
-            bool all = true;
-            for (float t : g.cand_ms) all &= t >= 0.f;
-            if (all) {
-                int best = 0;
-                for (size_t k = 1; k < g.cand_ms.size(); ++k)
-                    if (g.cand_ms[k] < g.cand_ms[best]) best = (int)k;
-                g.best = best;
-            }
+            tuner_record(g, cand, ms, sms);
         }
         if (e != cudaSuccess) rc = bfail(SHARP_ERR_CUDA, cudaGetErrorString(e));
     }
@@ -338,8 +407,45 @@ int sharp_batch_set_graphs(sharp_batch b, int enable) {
 int sharp_batch_tuned_grid(sharp_batch b, int m) {
     if (!b) return -1;
     for (auto& g : b->groups)
-        if (g.m == m) return g.best >= 0 ? g.candidates[g.best] : -1;
+        if (g.m == m) return g.tuned ? g.best.grid : -1;
     return -1;
+}
+
+int sharp_batch_tuned_shape(sharp_batch b, int m, int* grid, int* rows, int* stagger_ns) {
+    if (!b) return bfail(SHARP_ERR_INVALID_ARG, "batch is NULL");
+    for (auto& g : b->groups) {
+        if (g.m != m) continue;
+        if (!g.tuned) return bfail(SHARP_ERR_STATE, "the tuner has not finished for this frame size");
+        if (grid) *grid = g.best.grid;
+        if (rows) *rows = g.best.ch;
+        if (stagger_ns) *stagger_ns = g.best.stagger;
+        return SHARP_OK;
+    }
+    return bfail(SHARP_ERR_INVALID_ARG, "no scan of the batch has frames of size " + std::to_string(m));
+}
+
+int sharp_batch_set_shape(sharp_batch b, int m, int grid, int rows, int stagger_ns) {
+    if (!b) return bfail(SHARP_ERR_INVALID_ARG, "batch is NULL");
+    for (auto& g : b->groups) {
+        if (g.m != m) continue;
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const bool rows_ok = rows == 4 || rows == 8 || (rows == 16 && m != 256);
+        if (grid < 1 || grid > g.max_grid || !rows_ok || stagger_ns < 0 || stagger_ns > 100000)
+            return bfail(SHARP_ERR_INVALID_ARG, "launch shape outside the tuner's candidates");
+        cudaDeviceSynchronize();
+        drop_schedules(b);   // recorded graphs hold the old launches
+        g.best.grid = grid;
+        g.best.ch = rows;
+        g.best.stagger = stagger_ns;
+        g.tuned = true;
+        g.stage = 3;
+        g.cand.clear();
+        g.cand_ms.clear();
+        return SHARP_OK;
+    }
+    return bfail(SHARP_ERR_INVALID_ARG, "no scan of the batch has frames of size " + std::to_string(m));
 }
 
 int sharp_batch_destroy(sharp_batch b) {

@@ -205,6 +205,10 @@ inline cudaError_t launch_raar_m(int flags, const FrameArgs& a, cudaStream_t s) 
 // FP16 / BF16x3 contractions.
 template <int PREC>
 cudaError_t launch_mixed_prec(int mode, int flags, const FrameArgs& a, cudaStream_t s);
+// The same for 256^2 frames (raar_mixed256.cuh): the transforms split once,
+// radix 2, into four 128^2 sub-problems; `slab` holds m*m scratch per block.
+template <int PREC>
+cudaError_t launch_mixed256_prec(int mode, int flags, const FrameArgs& a, float2* slab, cudaStream_t s);
 cudaError_t launch_mixed(int prec, int mode, int flags, const FrameArgs& a, cudaStream_t s);  // sharp_api.cu
 
 // 256^2 frames (frame256_raar.cu, frame256_ops.cu): the RAAR pass for one
@@ -212,7 +216,7 @@ cudaError_t launch_mixed(int prec, int mode, int flags, const FrameArgs& a, cuda
 // one per block, at most one block per SM.
 struct BatchTable;
 cudaError_t launch_big_raar(int flags, const FrameArgs& a, const BatchTable* bt, int grid, float2* slab,
-                            cudaStream_t s);
+                            cudaStream_t s, int ch = 8);   // ch: rows of the pass-1 / pass-3 round trips (4, 8)
 cudaError_t launch_big_ops(int mode, const FrameArgs& a, cudaStream_t s);
 
 inline cudaError_t launch_frames(int mode, int flags, const FrameArgs& a, cudaStream_t s) {
@@ -282,9 +286,24 @@ struct BatchTable {
     int total;                // base[nscans]
     int* counter;             // global frame counter (zeroed per launch)
     int* err;                 // batch status; a timeout also sets the scan's plan flag
+    int stagger_ns;           // block b starts (b % 4) * stagger_ns after the launch (tile shape)
 };
-template <int M>
-cudaError_t launch_raar_batch_m(int flags, const BatchTable& bt, int grid, cudaStream_t s);
+// The batch frame pass of frame size M with CH rows per load / epilogue
+// round trip (64, 128: CH in {4, 8, 16}, one translation unit per pair).
+template <int M, int CH>
+cudaError_t launch_raar_batch_mc(int flags, const BatchTable& bt, int grid, cudaStream_t s);
+inline cudaError_t launch_raar_batch(int m, int ch, int flags, const BatchTable& bt, int grid, cudaStream_t s) {
+    if (m == 64) {
+        if (ch == 4) return launch_raar_batch_mc<64, 4>(flags, bt, grid, s);
+        if (ch == 8) return launch_raar_batch_mc<64, 8>(flags, bt, grid, s);
+        if (ch == 16) return launch_raar_batch_mc<64, 16>(flags, bt, grid, s);
+    } else if (m == 128) {
+        if (ch == 4) return launch_raar_batch_mc<128, 4>(flags, bt, grid, s);
+        if (ch == 8) return launch_raar_batch_mc<128, 8>(flags, bt, grid, s);
+        if (ch == 16) return launch_raar_batch_mc<128, 16>(flags, bt, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
 template <int M>
 cudaError_t raar_batch_max_grid(int* grid);
 

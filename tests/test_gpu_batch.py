@@ -139,3 +139,66 @@ def test_batch_rejects_mixed_cadence():
     amps = [dev(_amplitudes(a), torch.float32), dev(_amplitudes(b), torch.float32)]
     with pytest.raises(S.SharpError):
         S.Batch([pa, pb], amps)
+
+
+def test_every_tuner_candidate_gives_the_same_result():
+    """The batch autotuner only changes how frames are scheduled and loaded
+    (blocks per SM, rows per round trip of the gathers and the scatter, the
+    block-start stagger): every candidate shape steps the scans to the result
+    of the default shape within the rounding floor of the atomic sums (two
+    runs of the same shape), and the tuner's own choice is one of them."""
+    import paper_1602_01448_gb300 as S
+    scans = [synth.scan_batch_member(41, 64, 24), synth.scan_batch_member(42, 128, 10),
+             synth.scan_batch_member(43, 256, 5)]
+    amps = [dev(_amplitudes(sc), torch.float32) for sc in scans]
+    plans = [_start(S, sc) for sc in scans]
+    batch = S.Batch(plans, amps, use_graphs=False)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n_steps = 2
+
+    def run(shapes):
+        for p, sc in zip(plans, scans):
+            # restart in the buffers the batch is bound to
+            rng = np.random.default_rng(sc.seed + 2000)
+            psi0 = dev(synth.random_object(sc.shape, rng, phase_sigma=1.0))
+            w0 = dev(synth.perturb_probe(sc.probe, rng, 0.1))
+            S.sharp_raar_init(p.handle, psi0, w0, p.c, p.psi_y, p.psi)
+            p.probe.copy_(w0)
+        for m, shape in shapes.items():
+            batch.set_shape(m, *shape)
+        batch.iter = 0
+        for _ in range(n_steps):
+            batch.step()
+        batch.status()
+        return [host(p.psi) for p in plans]
+
+    default = {64: (sms, 8, 2000), 128: (sms, 8, 2000), 256: (sms, 8, 2000)}
+    ref = run(default)
+    again = run(default)
+    floor = [rel_l2(g, r) for g, r in zip(again, ref)]
+    cands = {64: [(k * sms, r, st) for k in (1, 2, 3) for r in (4, 8, 16) for st in (0, 2000)],
+             128: [(sms, r, st) for r in (4, 8, 16) for st in (0, 2000)],
+             256: [(sms, r, st) for r in (4, 8) for st in (0, 2000)]}
+    for m, shapes in cands.items():
+        for shape in shapes:
+            got = run({**default, m: shape})
+            k = [sc.m for sc in scans].index(m)
+            err = rel_l2(got[k], ref[k])
+            assert err < max(TOL * n_steps, 16.0 * floor[k]), (m, shape, err, floor[k])
+    with pytest.raises(S.SharpError):
+        batch.set_shape(256, sms, 16, 0)          # 16 rows: not a 256^2 candidate
+    with pytest.raises(S.SharpError):
+        batch.set_shape(32, sms, 8, 0)            # no scan of that size
+    batch.close()
+
+    # a fresh batch picks one of the candidates (tuned now, or earlier in the
+    # process for its frame size and size class)
+    plans2 = [_start(S, sc) for sc in scans]
+    b2 = S.Batch(plans2, amps, use_graphs=True)
+    for _ in range(8):
+        b2.step()
+    b2.status()
+    for m, shapes in cands.items():
+        shape = b2.tuned_shape(m)
+        assert shape in shapes, (m, shape)
+    b2.close()

@@ -215,14 +215,23 @@ def test_small_raster_nrmse_within_2_percent_of_oracle():
         assert r <= 1.02, (it, r, ratios)
 
 
+_AMP_CACHE = {}
+
+
 def _host_amplitudes(s, seed, chunk=500):
     """Amplitudes of the scan from the oracle's forward model (Eq. 1), with
-    5 % multiplicative noise, computed on the host in chunks of frames."""
+    5 % multiplicative noise, computed on the host in chunks of frames (kept
+    for the other tests of the same scan)."""
+    key = (s.name, s.seed, seed)
+    if key in _AMP_CACHE:
+        return _AMP_CACHE[key]
+    _AMP_CACHE.clear()
     rng = np.random.default_rng(seed)
     out = np.empty((s.K, s.m, s.m), np.float32)
     for k0 in range(0, s.K, chunk):
         a = O.forward_amplitudes(s.obj, s.probe, s.pos[k0:k0 + chunk], s.wrap)
         out[k0:k0 + chunk] = np.abs(a * (1.0 + 0.05 * rng.standard_normal(a.shape)))
+    _AMP_CACHE[key] = out
     return out
 
 
