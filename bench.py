@@ -44,9 +44,10 @@ sys.path.insert(0, ROOT)
 METRIC = "RAAR frame-iterations/s on 1 GB300 (FP32 vs mixed) and % of HBM roofline"
 UNIT = "frame-iterations/s"
 RESIDUAL_EVERY = 10   # eps_Q and eps_Delta every 10th step; eps_a every step
-FRAME_KERNEL = {"fermat": "raar_kernel<128>", "raster256": "big_kernel<RAAR> (256^2 line passes)"}
+FRAME_KERNEL = {"fermat": "raar_kernel<128>",
+                "raster256": "raar_split256_kernel (256^2 frames as four 128^2 register transforms)"}
 PROFILES = {"fermat": os.path.join(ROOT, "profiles", "raar_kernel_fermat128.txt"),
-            "raster256": os.path.join(ROOT, "profiles", "big_kernel_raster256.txt")}
+            "raster256": os.path.join(ROOT, "profiles", "raar_split256_raster256.txt")}
 CSRC = os.path.join(ROOT, "paper_1602_01448_gb300", "csrc")
 
 
@@ -55,7 +56,7 @@ CSRC = os.path.join(ROOT, "paper_1602_01448_gb300", "csrc")
 KERNEL_SOURCES = {
     "fermat": ["raar_kernel.cuh", "fft_frame.cuh", "tma.cuh", "sharp_common.cuh", "gen_twiddles.py",
                "raar_128_w0.cu"],
-    "raster256": ["frame256.cuh", "frame256_raar.cu", "fft_frame.cuh", "tma.cuh", "sharp_common.cuh",
+    "raster256": ["raar_split256.cuh", "raar_split256.cu", "fft_frame.cuh", "tma.cuh", "sharp_common.cuh",
                   "gen_twiddles.py"],
 }
 

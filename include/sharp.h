@@ -260,7 +260,7 @@ int sharp_amp_loss_backward(sharp_plan plan, const float2* obj, const float2* pr
  * step schedule is recorded as a CUDA graph on first use and replayed
  * afterwards.  The launch shape of each frame size is chosen by an autotuner
  * on the first steps: blocks per SM, rows per round trip of the frame pass's
- * gathers and scatter (4, 8, 16; 4, 8 for 256^2 frames) and the block-start
+ * gathers and scatter (4, 8, 16; 2, 4 for 256^2 frames) and the block-start
  * stagger, one parameter at a time, each candidate timed once; while it runs,
  * steps go without graphs and synchronise the stream.  The choice is kept for
  * the process per frame size and batch size class (frames rounded down to a

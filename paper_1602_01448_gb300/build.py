@@ -22,8 +22,9 @@ SOURCES = ["raar_128_w0.cu", "raar_128_w1.cu", "raar_64_w0.cu", "raar_64_w1.cu",
            "frame_kernels_64.cu", "image_kernels.cu", "sharp_api.cu", "noalloc.cu",
            "raar_batch_64_c4.cu", "raar_batch_64_c8.cu", "raar_batch_64_c16.cu",
            "raar_batch_128_c4.cu", "raar_batch_128_c8.cu", "raar_batch_128_c16.cu", "sharp_batch.cu",
-           "frame256_raar.cu", "frame256_ops.cu", "raar_mixed_fp16.cu", "raar_mixed_bf16.cu",
-           "raar_mixed256_fp16.cu", "raar_mixed256_bf16.cu"]
+           "frame256_ops.cu", "raar_mixed_fp16.cu", "raar_mixed_bf16.cu",
+           "raar_mixed256_fp16.cu", "raar_mixed256_bf16.cu", "raar_split256.cu",
+           "raar_split256_batch.cu"]
 
 
 def nvcc() -> str:

@@ -7,11 +7,11 @@ namespace sharp {
 
 cudaError_t launch_big_ops(int mode, const FrameArgs& a, cudaStream_t s) {
     switch (mode) {
-        case MODE_PROJECT: return big_launch<MODE_PROJECT, 0>(a, nullptr, 0, a.scratch, s);
-        case MODE_AMPS: return big_launch<MODE_AMPS, 0>(a, nullptr, 0, a.scratch, s);
-        case MODE_LOSS: return big_launch<MODE_LOSS, 0>(a, nullptr, 0, a.scratch, s);
-        case MODE_GRAD: return big_launch<MODE_GRAD, 0>(a, nullptr, 0, a.scratch, s);
-        case MODE_MASK: return big_launch<MODE_MASK, 0>(a, nullptr, 0, a.scratch, s);
+        case MODE_PROJECT: return big_launch<MODE_PROJECT>(a, a.scratch, s);
+        case MODE_AMPS: return big_launch<MODE_AMPS>(a, a.scratch, s);
+        case MODE_LOSS: return big_launch<MODE_LOSS>(a, a.scratch, s);
+        case MODE_GRAD: return big_launch<MODE_GRAD>(a, a.scratch, s);
+        case MODE_MASK: return big_launch<MODE_MASK>(a, a.scratch, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -10,7 +10,8 @@
 // The launch shape of each frame-size group is chosen online by a small
 // autotuner: the number of resident blocks per SM, the rows each thread loads
 // and stores per round trip of the gathers and the scatter (the frame pass's
-// tile shape: 4, 8 or 16 rows for 64^2 and 128^2 frames, 4 or 8 for 256^2),
+// tile shape: 4, 8 or 16 rows for 64^2 and 128^2 frames, 2 or 4 row pairs of
+// the four quadrants for 256^2),
 // and whether block starts are staggered.  The first steps time one
 // candidate each with events around the group's frame pass, one parameter
 // at a time (coordinate descent: grid, then rows, then stagger, each from the
@@ -92,7 +93,7 @@ bool next_stage(Group& g, int sms) {
                 g.cand.push_back(s);
             }
         } else if (g.stage == 1) {
-            for (int ch : (g.m == 256 ? std::vector<int>{4, 8} : std::vector<int>{4, 8, 16}))
+            for (int ch : (g.m == 256 ? std::vector<int>{2, 4} : std::vector<int>{4, 8, 16}))
                 if (ch != g.best.ch) {
                     Shape s = g.best;
                     s.ch = ch;
@@ -162,11 +163,7 @@ cudaError_t launch_group(const Group& g, const sharp::FrameArgs* table, int flag
     bt.counter = counter;
     bt.err = err;
     bt.stagger_ns = sh.stagger;
-    if (g.m == 256) {
-        sharp::FrameArgs none;
-        memset(&none, 0, sizeof(none));
-        return sharp::launch_big_raar(flags, none, &bt, sh.grid, g.slab, s, sh.ch);
-    }
+    if (g.m == 256) return sharp::launch_split256_batch(flags, bt, sh.grid, g.slab, s, sh.ch);
     return sharp::launch_raar_batch(g.m, sh.ch, flags, bt, sh.grid, s);
 }
 
@@ -226,6 +223,7 @@ int sharp_batch_create(sharp_batch* out, int nscans, const sharp_plan* plans) {
             return bfail(SHARP_ERR_CUDA, cudaGetErrorString(e));
         }
         g.best.grid = std::min(sms, g.max_grid);
+        g.best.ch = m == 256 ? 4 : 8;
         {
             std::lock_guard<std::mutex> lk(g_tuned_mutex);
             auto it = g_tuned.find({m, size_class(g.total)});
@@ -431,7 +429,7 @@ int sharp_batch_set_shape(sharp_batch b, int m, int grid, int rows, int stagger_
         int dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const bool rows_ok = rows == 4 || rows == 8 || (rows == 16 && m != 256);
+        const bool rows_ok = m == 256 ? (rows == 2 || rows == 4) : (rows == 4 || rows == 8 || rows == 16);
         if (grid < 1 || grid > g.max_grid || !rows_ok || stagger_ns < 0 || stagger_ns > 100000)
             return bfail(SHARP_ERR_INVALID_ARG, "launch shape outside the tuner's candidates");
         cudaDeviceSynchronize();

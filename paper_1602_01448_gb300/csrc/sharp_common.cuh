@@ -211,13 +211,15 @@ template <int PREC>
 cudaError_t launch_mixed256_prec(int mode, int flags, const FrameArgs& a, float2* slab, cudaStream_t s);
 cudaError_t launch_mixed(int prec, int mode, int flags, const FrameArgs& a, cudaStream_t s);  // sharp_api.cu
 
-// 256^2 frames (frame256_raar.cu, frame256_ops.cu): the RAAR pass for one
-// scan (bt null) or a batch, and the standalone modes; slabs of m*m scratch,
-// one per block, at most one block per SM.
-struct BatchTable;
-cudaError_t launch_big_raar(int flags, const FrameArgs& a, const BatchTable* bt, int grid, float2* slab,
-                            cudaStream_t s, int ch = 8);   // ch: rows of the pass-1 / pass-3 round trips (4, 8)
+// 256^2 frames, the standalone modes (frame256_ops.cu): line passes through
+// slabs of m*m scratch, one per block, at most one block per SM.
 cudaError_t launch_big_ops(int mode, const FrameArgs& a, cudaStream_t s);
+// The RAAR pass of 256^2 frames through four 128^2 register transforms
+// (raar_split256.cuh) for one scan, or for the scans of a batch with `ch`
+// rows per round trip (2, 4); `slab` holds m*m scratch per block.
+cudaError_t launch_split256(int flags, const FrameArgs& a, float2* slab, cudaStream_t s);
+struct BatchTable;
+cudaError_t launch_split256_batch(int flags, const BatchTable& bt, int grid, float2* slab, cudaStream_t s, int ch);
 
 inline cudaError_t launch_frames(int mode, int flags, const FrameArgs& a, cudaStream_t s) {
     if (a.K <= 0) return cudaSuccess;
@@ -225,8 +227,7 @@ inline cudaError_t launch_frames(int mode, int flags, const FrameArgs& a, cudaSt
         case 64: return launch_frames_m<64>(mode, flags, a, s);
         case 128: return launch_frames_m<128>(mode, flags, a, s);
         case 256:
-            return mode == MODE_RAAR ? launch_big_raar(flags, a, nullptr, 0, a.scratch, s)
-                                     : launch_big_ops(mode, a, s);
+            return mode == MODE_RAAR ? launch_split256(flags, a, a.scratch, s) : launch_big_ops(mode, a, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -83,6 +83,55 @@ __device__ __forceinline__ void tmem_st8x2(uint32_t ta, uint32_t tb, const float
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// N = 4 or 8 consecutive columns of this warp's 32 lanes, one value per
+// column: a store (wait with tmem_wait_st before reading back) and a load
+// completed before the asm ends.
+template <int N>
+__device__ __forceinline__ void tmem_st_cols(uint32_t ta, const float (&v)[N]) {
+    static_assert(N == 4 || N == 8, "4 or 8 columns");
+    if constexpr (N == 4) {
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(ta),
+                     "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                     "r"(__float_as_uint(v[3]))
+                     : "memory");
+    } else {
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta),
+                     "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                     "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                     "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                     : "memory");
+    }
+}
+// Two loads of N columns (at ta and tb), waited for.
+template <int N>
+__device__ __forceinline__ void tmem_ld_cols2(uint32_t ta, uint32_t tb, float (&a)[N], float (&b)[N]) {
+    static_assert(N == 4 || N == 8, "4 or 8 columns");
+    uint32_t r[2 * N];
+    if constexpr (N == 4) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%8];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%9];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+            : "r"(ta), "r"(tb)
+            : "memory");
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(ta), "r"(tb)
+            : "memory");
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        a[j] = __uint_as_float(r[j]);
+        b[j] = __uint_as_float(r[N + j]);
+    }
+}
+
 // ---------------------------------------------------------------- MMA
 // Shared-memory matrix descriptor: canonical K-major layout, no swizzle.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
