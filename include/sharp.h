@@ -218,6 +218,42 @@ int sharp_raar_step(sharp_plan plan, float2* state_c, float2* psi_y, float2* psi
                     cudaStream_t stream);
 
 /*
+ * Deterministic overlap sums.  By default the frame pass adds each frame's
+ * contribution to the overlap sums Q*(.) of Eq. 9 with atomic additions, so
+ * their FP32 rounding depends on the order in which frames finish and two
+ * runs differ at rounding level.  With enable != 0 the frame pass scatters
+ * nothing; the sums are gathered afterwards per 32 x 32 image tile over the
+ * frames covering it, in a fixed order (one more read of the frame state per
+ * step, and of the iterate on steps after a probe update), so the iterate,
+ * object and probe of every step are bit-identical from run to run.  The
+ * metrics are not: each block adds up its terms in FP32 over the frames it
+ * happened to take, so they differ at FP32 rounding (about 1e-7 relative).
+ * Single scans only
+ * (sharp_batch_create rejects such plans).  Errors: INVALID_ARG.
+ */
+int sharp_plan_set_deterministic(sharp_plan plan, int enable);
+
+/*
+ * Checkpoint and resume of a RAAR reconstruction (the state of Sec. 2.2's
+ * iteration).  The caller owns and saves state_c, psi_y and psi; the plan
+ * holds the current probe, the probe that formed the iterate and the step
+ * bookkeeping:
+ *   sharp_raar_checkpoint copies the two probes (DEVICE float2[m][m] each)
+ *   and fills info (HOST int[4]: last step run, whether the object equals
+ *   Q* z / Q*Q, whether the probe changed at the last step, 0);
+ *   sharp_raar_restore makes a plan over the same scan continue from such a
+ *   record (probes copied, Q*Q recomputed), after the caller has restored
+ *   state_c, psi_y and psi.  The next step must be info[0] + 1.  The buffer of
+ *   eps_Delta is not part of the record: the first step after a restore that
+ *   would read it reports eps_Delta as NaN.  With deterministic sums the
+ *   resumed steps are bit-identical to uninterrupted ones.
+ * Errors: INVALID_ARG, STATE (checkpoint before sharp_raar_init).
+ */
+int sharp_raar_checkpoint(sharp_plan plan, float2* probe_cur, float2* probe_form, int* info, cudaStream_t stream);
+int sharp_raar_restore(sharp_plan plan, const float2* probe_cur, const float2* probe_form, const int* info,
+                       cudaStream_t stream);
+
+/*
  * Solution metric eps_0 (Eq. 14) at z = Q psi, z0 = Q psi_true:
  *   out[0] = min_phi ||D (e^{i phi} psi - psi_true)|| / ||D psi_true||, D = Q*Q of `probe`;
  *   out[1] = object NRMSE over pixels with D >= 0.1 max D, same phase rule.

@@ -80,6 +80,9 @@ _lib_fns = {
     "sharp_plan_set_profiling": ([_P, _I], _I),
     "sharp_plan_status": ([_P, _P], _I),
     "sharp_plan_set_wait_limit": ([_P, ctypes.c_longlong], _I),
+    "sharp_plan_set_deterministic": ([_P, _I], _I),
+    "sharp_raar_checkpoint": ([_P, _P, _P, ctypes.POINTER(_I), _P], _I),
+    "sharp_raar_restore": ([_P, _P, _P, ctypes.POINTER(_I), _P], _I),
     "sharp_fourier_project_noalloc": ([_P, _P, _P, _P, _I, _I, _P], _I),
     "sharp_plan_set_probe_refinement": ([_P, _I, _P, _I, _P], _I),
     "sharp_probe_refine": ([_P, _P, _P, _P], _I),
@@ -289,6 +292,35 @@ class Plan:
         """Raise SharpError if a kernel of this plan flagged a failure (a bounded
         wait gave up, or invalid amplitudes or probe were seen)."""
         _check(_C["sharp_plan_status"](self.handle, _stream(stream)))
+
+    def set_deterministic(self, enable=True):
+        """Gather the overlap sums in a fixed order (bit-identical steps)."""
+        _check(_C["sharp_plan_set_deterministic"](self.handle, int(bool(enable))))
+
+    def checkpoint(self):
+        """Everything needed to resume the reconstruction (host copies)."""
+        pc = torch.empty((self.m, self.m), dtype=torch.complex64, device=self.device)
+        pf = torch.empty_like(pc)
+        info = (_I * 4)()
+        _check(_C["sharp_raar_checkpoint"](self.handle, _c64(pc, "probe_cur"), _c64(pf, "probe_form"), info,
+                                           _stream()))
+        torch.cuda.synchronize(self.device)
+        return {"c": self.c.cpu(), "psi_y": self.psi_y.cpu(), "psi": self.psi.cpu(), "probe": self.probe.cpu(),
+                "probe_cur": pc.cpu(), "probe_form": pf.cpu(), "info": list(info), "iter": self.iter}
+
+    def restore(self, ckpt):
+        """Continue from checkpoint() of a plan over the same scan."""
+        dev = self.device
+        self.c = ckpt["c"].to(dev).contiguous()
+        self.psi_y = ckpt["psi_y"].to(dev).contiguous()
+        self.psi = ckpt["psi"].to(dev).contiguous()
+        self.probe = ckpt["probe"].to(dev).contiguous()
+        info = (_I * 4)(*ckpt["info"])
+        pc = ckpt["probe_cur"].to(dev).contiguous()
+        pf = ckpt["probe_form"].to(dev).contiguous()
+        _check(_C["sharp_raar_restore"](self.handle, _c64(pc, "probe_cur"), _c64(pf, "probe_form"), info, _stream()))
+        torch.cuda.synchronize(dev)   # the copies out of pc and pf are done
+        self.iter = int(ckpt["iter"])
 
     def set_wait_limit(self, polls=-1):
         """Poll limit of the frame passes' bounded waits (-1: default, 0: give up at once)."""

@@ -153,6 +153,58 @@ overlap_gather_kernel(const int32_t* __restrict__ pos, const int* __restrict__ t
     }
 }
 
+// The overlap sums of the RAAR step relative to the object, gathered per
+// image tile over the frames covering it in a fixed order (the deterministic
+// mode of the frame pass, which then scatters nothing):
+//   out(x) = sum_i conj(w_p(r_i)) (u_i(r_i) - rho w_p(r_i) psi(x)),  r_i = x - x_i,
+// with u_i = c_i (the new state: C', rho = 1 - b) or u_i = w_f(r_i) psi_y(x)
+// + c_i (the iterate z before the step: B', rho = 1; w_f and psi_y given).
+// Terms are summed in FP32 with compensation, as Q* z above.
+__global__ void __launch_bounds__(GATHER_THREADS)
+overlap_delta_gather_kernel(const int32_t* __restrict__ pos, const int* __restrict__ tptr,
+                            const int* __restrict__ tfr, const float2* __restrict__ wp,
+                            const float2* __restrict__ wf, const float2* __restrict__ c,
+                            const float2* __restrict__ psiy, const float2* __restrict__ psi, float rho,
+                            float2* __restrict__ img, int m, int ny, int nx, int tiles_x, int wrap) {
+    const int tile = blockIdx.x;
+    const int gx = (tile % tiles_x) * TILE + (threadIdx.x & 31);
+    const int gy0 = (tile / tiles_x) * TILE + (threadIdx.x >> 5);
+    float sr[4] = {0.f, 0.f, 0.f, 0.f}, si[4] = {0.f, 0.f, 0.f, 0.f};
+    float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
+    float2 ps[4], py4[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int gy = gy0 + 8 * r;
+        const bool in = gy < ny && gx < nx;
+        ps[r] = in ? psi[gy * nx + gx] : make_float2(0.f, 0.f);
+        py4[r] = (in && psiy) ? psiy[gy * nx + gx] : make_float2(0.f, 0.f);
+    }
+    const size_t mm = (size_t)m * m;
+    for (int j = tptr[tile]; j < tptr[tile + 1]; ++j) {
+        const int f = tfr[j];
+        const int py = pos[2 * f], px = pos[2 * f + 1];
+        const int lx = local_offset(gx, px, nx, wrap, m);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int ly = local_offset(gy0 + 8 * r, py, ny, wrap, m);
+            if (lx < m && ly < m) {
+                const int l = ly * m + lx;
+                const float2 w = __ldg(wp + l);
+                float2 u = __ldg(c + f * mm + l);
+                if (wf) u = cadd(u, cmul(__ldg(wf + l), py4[r]));
+                const float2 t = cmulc(w, csub(u, cscale(cmul(w, ps[r]), rho)));
+                kahan_add(sr[r], cr[r], t.x);
+                kahan_add(si[r], ci[r], t.y);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int gy = gy0 + 8 * r;
+        if (gy < ny && gx < nx) img[gy * nx + gx] = make_float2(sr[r], si[r]);
+    }
+}
+
 __global__ void scale_invd_kernel(float2* __restrict__ img, const float* __restrict__ invD, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         img[i] = cscale(img[i], invD[i]);
@@ -589,6 +641,14 @@ cudaError_t launch_overlap_gather(const Plan& p, const float2* probe, const floa
                                   cudaStream_t s) {
     overlap_gather_kernel<<<p.tiles_y * p.tiles_x, GATHER_THREADS, 0, s>>>(
         p.pos, p.tile_ptr, p.tile_frames, probe, z, img, p.m, p.ny, p.nx, p.tiles_x, p.prm.wrap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_overlap_delta_gather(const Plan& p, const float2* wp, const float2* wf, const float2* c,
+                                        const float2* psiy, const float2* psi, float rho, float2* img,
+                                        cudaStream_t s) {
+    overlap_delta_gather_kernel<<<p.tiles_y * p.tiles_x, GATHER_THREADS, 0, s>>>(
+        p.pos, p.tile_ptr, p.tile_frames, wp, wf, c, psiy, psi, rho, img, p.m, p.ny, p.nx, p.tiles_x, p.prm.wrap);
     return cudaGetLastError();
 }
 

@@ -92,11 +92,13 @@ __device__ __forceinline__ void raar_load_phase(const FrameArgs& a, int py, int 
             }
         }
         if constexpr (FLAGS & RF_FORM_B) {
+            if (!a.no_scatter) {
 #pragma unroll
-            for (int k = k0; k < k0 + CH; ++k) {
-                const int y = q + TX * k;
-                const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
-                red_hint(a.accB + o, cmulc(wp[k - k0], csub(v[k], cmul(wp[k - k0], pv[k - k0]))), pol_keep);
+                for (int k = k0; k < k0 + CH; ++k) {
+                    const int y = q + TX * k;
+                    const int o = obj_index(py, px, y, x, a.ny, a.nx, WRAP);
+                    red_hint(a.accB + o, cmulc(wp[k - k0], csub(v[k], cmul(wp[k - k0], pv[k - k0]))), pol_keep);
+                }
             }
         }
         if (a.write_e) {
@@ -164,7 +166,7 @@ __device__ __forceinline__ void raar_epilogue(const FrameArgs& a, int py, int px
             const float2 cn = v[k];
             st_hint(a.c + fo + y * M + x, cn, pol_stream);
             const float2 dn = csub(cn, cscale(cmul(wp[k - k0], pv[k - k0]), rho));
-            red_hint(a.accA + o, cmulc(wp[k - k0], dn), pol_keep);
+            if (!a.no_scatter) red_hint(a.accA + o, cmulc(wp[k - k0], dn), pol_keep);
             if (a.write_e) red_hint(a.ebuf + fo + y * M + x, cn, pol_stream);
         }
         chunk_fence_r();

@@ -461,7 +461,8 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                         }
                         if constexpr (FLAGS & RF_FORM_B) {
                             const int o = obj_index(py, px, y, xcol, a.ny, a.nx, WRAP);
-                            red_hint(a.accB + o, cmulc(wp[k], csub(z, cmul(wp[k], pv[k]))), pol_keep);
+                            if (!a.no_scatter)
+                                red_hint(a.accB + o, cmulc(wp[k], csub(z, cmul(wp[k], pv[k]))), pol_keep);
                         }
                         if (a.write_e) st_hint(a.ebuf + fo + y * M + xcol, make_float2(-z.x, -z.y), pol_stream);
                     }
@@ -579,8 +580,9 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                                 const int o = obj_index(py, px, y, xcol, a.ny, a.nx, WRAP);
                                 const float2 cn = make_float2(re[t] * inv, im[t] * inv);
                                 st_hint(a.c + fo + y * M + xcol, cn, pol_stream);
-                                red_hint(a.accA + o, cmulc(wp[k], csub(cn, cscale(cmul(wp[k], pv[k]), rho))),
-                                         pol_keep);
+                                if (!a.no_scatter)
+                                    red_hint(a.accA + o, cmulc(wp[k], csub(cn, cscale(cmul(wp[k], pv[k]), rho))),
+                                             pol_keep);
                                 if (a.write_e) red_hint(a.ebuf + fo + y * M + xcol, cn, pol_stream);
                             }
                         }

@@ -162,7 +162,8 @@ __global__ void __launch_bounds__(512, 1) raar_mixed256_kernel(const FrameArgs a
                             }
                             if constexpr (FLAGS & RF_FORM_B) {
                                 const int o = obj_index(py, px, y, xx, a.ny, a.nx, WRAP);
-                                red_hint(a.accB + o, cmulc(wp[pq], csub(z[pq], cmul(wp[pq], pv[pq]))), pol_keep);
+                                if (!a.no_scatter)
+                                    red_hint(a.accB + o, cmulc(wp[pq], csub(z[pq], cmul(wp[pq], pv[pq]))), pol_keep);
                             }
                             if (a.write_e)
                                 st_hint(a.ebuf + fo + y * M + xx, make_float2(-z[pq].x, -z[pq].y), pol_stream);
@@ -330,8 +331,9 @@ __global__ void __launch_bounds__(512, 1) raar_mixed256_kernel(const FrameArgs a
                                 const int o = obj_index(py, px, y, xx, a.ny, a.nx, WRAP);
                                 st_hint(a.c + fo + y * M + xx, cn[pq], pol_stream);
                                 // C' += conj(w) (c_new - (1-b) w psi), relative to the object
-                                red_hint(a.accA + o, cmulc(wp[pq], csub(cn[pq], cscale(cmul(wp[pq], pv[pq]), rho))),
-                                         pol_keep);
+                                if (!a.no_scatter)
+                                    red_hint(a.accA + o, cmulc(wp[pq], csub(cn[pq], cscale(cmul(wp[pq], pv[pq]), rho))),
+                                             pol_keep);
                                 if (a.write_e) red_hint(a.ebuf + fo + y * M + xx, cn[pq], pol_stream);
                             }
                         } else {

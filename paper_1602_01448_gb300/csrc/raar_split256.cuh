@@ -203,8 +203,9 @@ raar_split256_kernel(const FrameArgs ap, const BatchTable bt, float2* slab) {
                         if constexpr (FLAGS & RF_FORM_B) {
                             // B' = Q*(z - w psi), relative to the object (image pass)
                             const int o = obj_index(py, px, y, x, a.ny, a.nx, wrap);
-                            red_hint(a.accB + o, cmulc(wp[kk][pq], csub(z[pq], cmul(wp[kk][pq], pv[kk][pq]))),
-                                     pol_keep);
+                            if (!a.no_scatter)
+                                red_hint(a.accB + o, cmulc(wp[kk][pq], csub(z[pq], cmul(wp[kk][pq], pv[kk][pq]))),
+                                         pol_keep);
                         }
                         if (a.write_e) st_hint(a.ebuf + fo + y * M + x, make_float2(-z[pq].x, -z[pq].y), pol_stream);
                     }
@@ -335,8 +336,10 @@ raar_split256_kernel(const FrameArgs ap, const BatchTable bt, float2* slab) {
                         const int o = obj_index(py, px, y, x, a.ny, a.nx, wrap);
                         st_hint(a.c + fo + y * M + x, cn[pq], pol_stream);
                         // C' += conj(w) (c_new - (1-b) w psi), relative to the object
-                        red_hint(a.accA + o, cmulc(wp[kk][pq], csub(cn[pq], cscale(cmul(wp[kk][pq], pv[kk][pq]), rho))),
-                                 pol_keep);
+                        if (!a.no_scatter)
+                            red_hint(a.accA + o,
+                                     cmulc(wp[kk][pq], csub(cn[pq], cscale(cmul(wp[kk][pq], pv[kk][pq]), rho))),
+                                     pol_keep);
                         if (a.write_e) red_hint(a.ebuf + fo + y * M + x, cn[pq], pol_stream);
                     }
                 }

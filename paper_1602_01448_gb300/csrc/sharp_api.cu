@@ -210,6 +210,7 @@ int sharp::raar_step_prepare(Plan& p, float2* state_c, float2* psi_y, float2* ps
     a.amp = amp;
     a.read_e = in.read_e;
     a.write_e = in.write_e;
+    a.no_scatter = p.deterministic;
     *out = a;
     *info = in;
     return SHARP_OK;
@@ -423,6 +424,48 @@ int sharp_plan_status(sharp_plan plan, cudaStream_t s) {
     return SHARP_OK;
 }
 
+int sharp_plan_set_deterministic(sharp_plan plan, int enable) {
+    if (int r = check_plan(plan)) return r;
+    plan->p.deterministic = enable ? 1 : 0;
+    return SHARP_OK;
+}
+
+int sharp_raar_checkpoint(sharp_plan plan, float2* probe_cur, float2* probe_form, int* info, cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    SHARP_NONNULL(probe_cur); SHARP_NONNULL(probe_form); SHARP_NONNULL(info);
+    Plan& p = plan->p;
+    if (!p.initialised) return fail(SHARP_ERR_STATE, "checkpoint before sharp_raar_init");
+    const size_t mm = (size_t)p.m * p.m;
+    SHARP_CK(cudaMemcpyAsync(probe_cur, p.w_cur, mm * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    SHARP_CK(cudaMemcpyAsync(probe_form, p.w_form, mm * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    info[0] = p.last_iter;
+    info[1] = p.b_valid ? 1 : 0;
+    info[2] = p.form_differs ? 1 : 0;
+    info[3] = 0;
+    return SHARP_OK;
+}
+
+int sharp_raar_restore(sharp_plan plan, const float2* probe_cur, const float2* probe_form, const int* info,
+                       cudaStream_t s) {
+    if (int r = check_plan(plan)) return r;
+    SHARP_NONNULL(probe_cur); SHARP_NONNULL(probe_form); SHARP_NONNULL(info);
+    Plan& p = plan->p;
+    if (info[0] < 0 || (info[1] != 0 && info[1] != 1) || (info[2] != 0 && info[2] != 1))
+        return fail(SHARP_ERR_INVALID_ARG, "checkpoint record out of range");
+    const size_t n = (size_t)p.ny * p.nx, mm = (size_t)p.m * p.m;
+    SHARP_CK(cudaMemcpyAsync(p.w_cur, probe_cur, mm * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    SHARP_CK(cudaMemcpyAsync(p.w_form, probe_form, mm * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    SHARP_CK(sharp::launch_illumination(p, p.w_cur, p.w2, p.Dsum, p.invD, p.dmax_bits, s));
+    SHARP_CK(cudaMemsetAsync(p.accA, 0, n * sizeof(float2), s));
+    SHARP_CK(cudaMemsetAsync(p.accB, 0, n * sizeof(float2), s));
+    p.last_iter = info[0];
+    p.b_valid = info[1] != 0;
+    p.form_differs = info[2] != 0;
+    p.e_written_iter = 0;   // the eps_Delta buffer is not part of a checkpoint
+    p.initialised = true;
+    return SHARP_OK;
+}
+
 int sharp_plan_set_wait_limit(sharp_plan plan, long long polls) {
     if (int r = check_plan(plan)) return r;
     if (polls > 0xfffffffeLL) return fail(SHARP_ERR_INVALID_ARG, "wait limit %lld above 2^32 - 2 polls", polls);
@@ -589,10 +632,24 @@ int sharp_raar_step(sharp_plan plan, float2* state_c, float2* psi_y, float2* psi
     sharp::StepInfo info;
     if (int r = sharp::raar_step_prepare(p, state_c, psi_y, psi, amp, iter, &a, &info)) return r;
     SHARP_CK(sharp::raar_step_clear(p, s));
+    if (p.deterministic && (info.flags & sharp::RF_FORM_B)) {
+        // B' = Q*(z - w psi) from the iterate entering the step (the frame
+        // pass overwrites its state)
+        SHARP_CK(timed(p, K_OTHER, 1, s, [&] {
+            return sharp::launch_overlap_delta_gather(p, p.w_cur, p.w_form, state_c, psi_y, psi, 1.f, p.accB, s);
+        }));
+    }
     SHARP_CK(timed(p, K_FRAME, 1, s, [&] {
         return mixed(p) ? sharp::launch_mixed(p.prm.precision, sharp::MODE_RAAR, info.flags, a, s)
                         : sharp::launch_frames(sharp::MODE_RAAR, info.flags, a, s);
     }));
+    if (p.deterministic) {
+        // C' = Q*(c_new - (1-b) w psi) from the new state
+        SHARP_CK(timed(p, K_OTHER, 1, s, [&] {
+            return sharp::launch_overlap_delta_gather(p, p.w_cur, nullptr, state_c, nullptr, psi,
+                                                      1.f - p.prm.beta, p.accA, s);
+        }));
+    }
     return sharp::raar_step_finish(p, state_c, psi_y, psi, probe, metrics, iter, info, s, true);
 }
 

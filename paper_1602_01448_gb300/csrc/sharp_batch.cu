@@ -190,6 +190,8 @@ int sharp_batch_create(sharp_batch* out, int nscans, const sharp_plan* plans) {
             return bfail(SHARP_ERR_INVALID_ARG, "plans of a batch must share probe_every and residual_every");
         if (pi.precision != SHARP_PREC_FP32)
             return bfail(SHARP_ERR_INVALID_ARG, "batched scans run in SHARP_PREC_FP32 only");
+        if (plans[i]->p.deterministic)
+            return bfail(SHARP_ERR_INVALID_ARG, "batched scans scatter their overlap sums (no deterministic mode)");
     }
     sharp_batch b = new sharp_batch_s;
     b->plans.assign(plans, plans + nscans);

@@ -146,6 +146,9 @@ struct Plan {
     void* dft_tab;
     // poll limit of the frame passes' bounded waits (FrameArgs::spin encoding)
     unsigned wait_spin;
+    // deterministic overlap sums: gathered per tile in a fixed order instead
+    // of scattered with atomics (bit-identical steps)
+    int deterministic;
 };
 
 constexpr int TILE = 32;
@@ -186,6 +189,7 @@ struct FrameArgs {
     float2* scratch;         // 256^2 frames: one m*m slab per block of the frame kernels
     const void* dft_tab;     // tensor-core precision modes: DFT matrix parts (raar_mixed.cuh layout)
     unsigned spin;           // poll limit of the first bounded waits (wait_polls: 0 default, kNoPolls none)
+    int no_scatter;          // deterministic mode: the overlap sums are gathered after the pass instead
 };
 
 // compile-time flags of MODE_RAAR
@@ -241,6 +245,12 @@ cudaError_t launch_q_gather(const Plan& p, const float2* obj, const float2* prob
 cudaError_t launch_overlap_gather(const Plan& p, const float2* probe, const float2* z, float2* img,
                                   cudaStream_t s);   // Q* z
 cudaError_t launch_scale_invD(const Plan& p, float2* img, const float* invD, cudaStream_t s);  // img *= invD
+// Deterministic overlap sums relative to the object (per-tile gathers in a
+// fixed frame order): img = sum_i conj(wp) (u_i - rho wp psi), u_i = c_i, or
+// wf psi_y + c_i when wf and psiy are given.
+cudaError_t launch_overlap_delta_gather(const Plan& p, const float2* wp, const float2* wf, const float2* c,
+                                        const float2* psiy, const float2* psi, float rho, float2* img,
+                                        cudaStream_t s);
 cudaError_t launch_probe_update_state(Plan& p, const float2* c, const float2* psiy, const float2* psi,
                                       cudaStream_t s);  // Eq. 10 on z = w_cur psiy + c -> w_cur
 cudaError_t launch_probe_update_frames(Plan& p, const float2* obj, const float2* z,
