@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         {
             const float inv = 1.f / (g0 * g1);   // exact: powers of two
             float um = 0.f;
-#pragma unroll
+#pragma unroll 1
             for (int j = 0; j < 2; ++j) {
 #pragma unroll
                 for (int s = 0; s < CW / 16; ++s) {
@@ -509,9 +509,8 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                     float av[16];
 #pragma unroll
                     for (int t = 0; t < 16; ++t) av[t] = __ldcs(a.amp + fo + (size_t)(k0 + t) * M + xcol);
-                    float ur[16], ui[16];
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) {
+                    for (int t = 0; t < 16; ++t) {   // U in place of Z
                         const float X = re[t] * inv, Y = im[t] * inv;
                         const float m2 = fmaf(X, X, Y * Y);
                         const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
@@ -521,20 +520,20 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                         bad |= (int)bad_amplitude(av[t]);
                         if (m2 > 0.f) {
                             const float f = fmaf(cp * av[t], rs, b);
-                            ur[t] = X * f;
-                            ui[t] = Y * f;
+                            re[t] = X * f;
+                            im[t] = Y * f;
                         } else {
-                            ur[t] = cp * av[t];
-                            ui[t] = 0.f;
+                            re[t] = cp * av[t];
+                            im[t] = 0.f;
                         }
-                        um = fmaxf(um, fmaxf(fabsf(ur[t]), fabsf(ui[t])));
+                        um = fmaxf(um, fmaxf(fabsf(re[t]), fabsf(im[t])));
                     }
                     float r8[8], i8[8];
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) { r8[t] = ur[t]; i8[t] = ui[t]; }
+                    for (int t = 0; t < 8; ++t) { r8[t] = re[t]; i8[t] = im[t]; }
                     tmem_st8x2(x.tl + RA + k0, x.tl + RA + 128 + k0, r8, i8);
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) { r8[t] = ur[8 + t]; i8[t] = ui[8 + t]; }
+                    for (int t = 0; t < 8; ++t) { r8[t] = re[8 + t]; i8[t] = im[8 + t]; }
                     tmem_st8x2(x.tl + RA + k0 + 8, x.tl + RA + 128 + k0 + 8, r8, i8);
                 }
             }
@@ -556,7 +555,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         if constexpr (G::STAGE) st_pending = i + (int)gridDim.x < a.K;
         {
             const float inv = 1.f / (g2 * g3);
-#pragma unroll
+#pragma unroll 1
             for (int j = 0; j < 2; ++j) {
 #pragma unroll
                 for (int s = 0; s < CW / 16; ++s) {
@@ -567,15 +566,17 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                         {
                             // C' += conj(w) (c_new - (1-b) w psi), relative to the object
                             const float rho = 1.f - a.beta;
-                            float2 wp[16], pv[16];
 #pragma unroll
-                            for (int k = 0; k < 16; ++k) {
-                                wp[k] = ld_hint(a.w_proj + (y0 + k) * M + xcol, pol_keep);
-                                pv[k] = ld_hint(a.psi + obj_index(py, px, y0 + k, xcol, a.ny, a.nx, WRAP), pol_keep);
+                            for (int hf = 0; hf < 2; ++hf) {
+                            float2 wp[8], pv[8];
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                wp[k] = ld_hint(a.w_proj + (y0 + 8 * hf + k) * M + xcol, pol_keep);
+                                pv[k] = ld_hint(a.psi + obj_index(py, px, y0 + 8 * hf + k, xcol, a.ny, a.nx, WRAP), pol_keep);
                             }
 #pragma unroll
-                            for (int k = 0; k < 16; ++k) {
-                                const int t = k;
+                            for (int k = 0; k < 8; ++k) {
+                                const int t = 8 * hf + k;
                                 const int y = y0 + t;
                                 const int o = obj_index(py, px, y, xcol, a.ny, a.nx, WRAP);
                                 const float2 cn = make_float2(re[t] * inv, im[t] * inv);
@@ -584,6 +585,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                                     red_hint(a.accA + o, cmulc(wp[k], csub(cn, cscale(cmul(wp[k], pv[k]), rho))),
                                              pol_keep);
                                 if (a.write_e) red_hint(a.ebuf + fo + y * M + xcol, cn, pol_stream);
+                            }
                             }
                         }
                     } else {
