@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed256_kernel(const FrameArgs a
                 const float inv = 0.5f / (g0 * g1);   // exact: powers of two
                 float um = 0.f;
                 const int kx = 2 * nu2 + sb;
-#pragma unroll
+#pragma unroll 1
                 for (int j = 0; j < 2; ++j) {
 #pragma unroll
                     for (int s = 0; s < CW / 16; ++s) {
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed256_kernel(const FrameArgs a
             const float inv = 1.f / (g2 * g3);
 
             if (sub < 3) {   // F128^-1(U_ab) into slab slot sub (its y_ab is consumed)
-#pragma unroll
+#pragma unroll 1
                 for (int j = 0; j < 2; ++j) {
 #pragma unroll
                     for (int s = 0; s < CW / 16; ++s) {
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed256_kernel(const FrameArgs a
 
             // ------------------------------------------ combination + epilogue
             if (x.leader) prefetch_frame(i + gridDim.x);
-#pragma unroll
+#pragma unroll 1
             for (int j = 0; j < 2; ++j) {
 #pragma unroll
                 for (int s = 0; s < CW / 16; ++s) {
