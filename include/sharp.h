@@ -123,7 +123,7 @@ int sharp_q_gather(sharp_plan plan, const float2* obj, const float2* probe,
  * phase 1 where F z = 0.  in-place (out == z) is allowed.
  *   z, out   : float2[K][m][m];  amp : float[K][m][m] (unitary scale).
  *   resid_sq : DEVICE double[1] or NULL; receives ||P_a z - z||^2 (overwritten).
- * In the tensor-core precision modes z must be 16-byte aligned (INVALID_ARG).
+ * In the tensor-core precision modes z and amp must be 16-byte aligned (INVALID_ARG).
  */
 int sharp_fourier_project(sharp_plan plan, const float2* z, const float* amp,
                           float2* out, double* resid_sq, cudaStream_t stream);

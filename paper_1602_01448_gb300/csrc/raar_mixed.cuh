@@ -321,6 +321,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     __shared__ FrameArgs a;
     __shared__ __align__(8) uint64_t bar;    // MMAs completed
     __shared__ __align__(8) uint64_t cbar;   // staged frame input arrived
+    __shared__ __align__(8) uint64_t abar;   // staged amplitudes arrived
     __shared__ uint32_t s_tmem;
     __shared__ float s_max[16];
     __shared__ float red[32 * 5];
@@ -347,6 +348,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         a = ap;
         mbar_init(&bar, 1);
         mbar_init(&cbar, 1);
+        mbar_init(&abar, 1);
         mbar_fence_init();
     }
     if (warp == 0) {
@@ -384,6 +386,13 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     // copies of 64 rows) at the same point, and the load phase reads it there.
     unsigned cpar = 0;
     bool st_pending = false;                  // uniform across the block
+    // FP16S also stages the frame's amplitudes (64 KB) in the first staging
+    // buffer, free from the end of the load phase to the next frame's input
+    // copy, by one bulk copy issued before the forward contractions, so the
+    // Fourier step reads them from shared memory.
+    float* const stage_amp = reinterpret_cast<float*>(const_cast<float2*>(stage_lo));
+    unsigned apar = 0;
+    bool am_pending = false;                  // uniform across the block
     auto stage_frame = [&](int f) {           // leader only
         const float2* src = (RAAR ? a.c : a.zin) + (size_t)f * MM;
         mbar_expect_tx(&cbar, (unsigned)(MM * sizeof(float2)));
@@ -487,6 +496,13 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         tmem_wait_st();
         float g0 = 1.f, g1 = 1.f, g2 = 1.f, g3 = 1.f;
         if constexpr (G::F16) g0 = mix_pow2_scale(mix_block_max<PREC>(x, mx));
+        if constexpr (G::STAGE) {   // every thread has read its staged input (block max above)
+            if (x.leader) {
+                mbar_expect_tx(&abar, (unsigned)(MM * sizeof(float)));
+                bulk_g2s_hint(stage_amp, a.amp + fo, (unsigned)(MM * sizeof(float)), &abar, pol_stream);
+            }
+            am_pending = true;
+        }
 
         // ------------------------------------------------ forward transform
         ok = mix_stage<PREC>(x, RA, RB, false, g0);
@@ -499,6 +515,12 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         {
             const float inv = 1.f / (g0 * g1);   // exact: powers of two
             float um = 0.f;
+            if constexpr (G::STAGE) {
+                ok = __syncthreads_and(mbar_wait(&abar, apar, x.polls));
+                if (!ok) break;
+                apar ^= 1u;
+                am_pending = false;
+            }
 #pragma unroll 1
             for (int j = 0; j < 2; ++j) {
 #pragma unroll
@@ -508,7 +530,8 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
                     tmem_ld16x2(x.tl + RA + k0, x.tl + RA + 128 + k0, re, im);
                     float av[16];
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) av[t] = __ldcs(a.amp + fo + (size_t)(k0 + t) * M + xcol);
+                    for (int t = 0; t < 16; ++t)
+                        av[t] = G::STAGE ? stage_amp[(k0 + t) * M + xcol] : __ldcs(a.amp + fo + (size_t)(k0 + t) * M + xcol);
 #pragma unroll
                     for (int t = 0; t < 16; ++t) {   // U in place of Z
                         const float X = re[t] * inv, Y = im[t] * inv;
@@ -606,6 +629,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
     // that nothing writes TMEM or shared memory after the block has left.
     if (x.mma_pending && x.leader) mbar_wait(x.bar, x.phase);
     if (st_pending && x.leader) mbar_wait(&cbar, cpar);
+    if (am_pending && x.leader) mbar_wait(&abar, apar);
     const bool all_ok = __syncthreads_and(ok);
     if (!all_ok) {
         if (tid == 0) atomicExch(a.err, SHARP_ERR_TIMEOUT);   // flag the failure, leave the sums alone

@@ -538,8 +538,8 @@ int sharp_fourier_project(sharp_plan plan, const float2* z, const float* amp, fl
     a.zin = z;
     a.zout = out;
     a.amp = amp;
-    if (mixed(p) && (reinterpret_cast<uintptr_t>(z) & 15))
-        return fail(SHARP_ERR_INVALID_ARG, "z must be 16-byte aligned in the tensor-core modes (bulk copies)");
+    if (mixed(p) && ((reinterpret_cast<uintptr_t>(z) | reinterpret_cast<uintptr_t>(amp)) & 15))
+        return fail(SHARP_ERR_INVALID_ARG, "z and amp must be 16-byte aligned in the tensor-core modes (bulk copies)");
     if (mixed(p)) SHARP_CK(sharp::launch_mixed(p.prm.precision, sharp::MODE_PROJECT, 0, a, s));
     else SHARP_CK(sharp::launch_frames(sharp::MODE_PROJECT, 0, a, s));
     if (resid_sq) SHARP_CK(sharp::launch_copy_scaled(p.sums, resid_sq, 1.0, s));
