@@ -55,9 +55,12 @@ extern "C" {
  * of Eq. 2 on the tensor cores, FP32 accumulation (a 256-point transform is
  * split once, radix 2, into 128-point ones); data, metrics and every other
  * operator stay FP32 / FP64.
- *   SHARP_PREC_FP16S  : FP16 operands; each operand matrix is scaled per frame
- *                       by a power of two (its largest component mapped into
- *                       [2^14, 2^15)) so that FP16's range is never left.
+ *   SHARP_PREC_FP16S  : FP16 operands scaled per frame by powers of two so
+ *                       that FP16's range is never left: each transform's
+ *                       input by the one that maps its largest component into
+ *                       [2^14, 2^15), the intermediate between the
+ *                       transform's two contractions by 2^-4 (its components
+ *                       are at most 16 times the input's largest).
  *                       Relative error of one transform ~1e-3 (RMS ~3e-4).
  *   SHARP_PREC_BF16X3 : BF16 operands split x = hi + lo, three products
  *                       hi.hi + hi.lo + lo.hi per real product.  Relative

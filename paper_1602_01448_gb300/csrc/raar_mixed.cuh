@@ -1,9 +1,16 @@
 // RAAR frame pass with the frame transforms as DFT-matrix contractions on the
 // fifth-generation tensor cores (tcgen05, TMEM accumulators), 128 x 128
 // frames, in two mixed-precision modes:
-//   SHARP_PREC_FP16S  : FP16 operands, each operand matrix scaled per frame by
-//                       a power of two (its largest component maps into
-//                       [2^14, 2^15)), one product per real matrix product;
+//   SHARP_PREC_FP16S  : FP16 operands scaled per frame by powers of two, one
+//                       product per real matrix product: the input of each
+//                       transform so that its largest component maps into
+//                       [2^14, 2^15), the input of the transform's second
+//                       contraction by 2^-4 (a component of a unitary
+//                       128-point transform is at most sqrt(2 * 128) = 16
+//                       times the largest input component, so the operand
+//                       stays below 2^15 with no pass over the intermediate;
+//                       FP16 rounding is relative, so the smaller range costs
+//                       no precision);
 //   SHARP_PREC_BF16X3 : BF16 operands split x = hi + lo, three products
 //                       hi.hi + hi.lo + lo.hi per real matrix product;
 // both accumulated in FP32 in tensor memory.
@@ -90,6 +97,11 @@ struct MixGeo {
     static_assert(CW % 16 == 0, "TMEM accesses of 16 columns");
 };
 
+
+// FP16S scale of the second contraction of a transform: its operand is the
+// first contraction's output, whose components are at most 16 times the
+// largest (scaled, < 2^15) input component.
+constexpr float kMixStage2Scale = 0.0625f;
 
 // Power of two 2^e with mx 2^e in [2^14, 2^15) (1 for 0, Inf or NaN).
 __device__ __forceinline__ float mix_pow2_scale(float mx) {
@@ -235,25 +247,6 @@ __device__ __forceinline__ void mix_convert(const MixCtx& x, uint32_t src, int j
         tmem_ld16x2(x.tl + src + c + 16 * s, x.tl + src + 128 + c + 16 * s, re, im);
         mix_put16<PREC>(sb, x.r, (G::CW / 8) * x.h + 2 * s, re, im, g);
     }
-}
-
-// Largest component of region `src` over the block.
-template <int PREC>
-__device__ __forceinline__ float mix_region_max(const MixCtx& x, uint32_t src) {
-    using G = MixGeo<PREC>;
-    float mx = 0.f;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const int c = mix_col<PREC>(j, x.h);
-#pragma unroll
-        for (int s = 0; s < G::CW / 16; ++s) {
-            float re[16], im[16];
-            tmem_ld16x2(x.tl + src + c + 16 * s, x.tl + src + 128 + c + 16 * s, re, im);
-#pragma unroll
-            for (int t = 0; t < 16; ++t) mx = fmaxf(mx, fmaxf(fabsf(re[t]), fabsf(im[t])));
-        }
-    }
-    return mix_block_max<PREC>(x, mx);
 }
 
 // Wait (bounded) for the issued MMAs; false if the wait gave up.  The leader
@@ -507,7 +500,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         // ------------------------------------------------ forward transform
         ok = mix_stage<PREC>(x, RA, RB, false, g0);
         if (!ok) break;
-        if constexpr (G::F16) g1 = mix_pow2_scale(mix_region_max<PREC>(x, RB));
+        if constexpr (G::F16) g1 = kMixStage2Scale;
         ok = mix_stage<PREC>(x, RB, RA, false, g1);
         if (!ok) break;
 
@@ -567,7 +560,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) 
         // ------------------------------------------------ inverse transform
         ok = mix_stage<PREC>(x, RA, RB, true, g2);
         if (!ok) break;
-        if constexpr (G::F16) g3 = mix_pow2_scale(mix_region_max<PREC>(x, RB));
+        if constexpr (G::F16) g3 = kMixStage2Scale;
         ok = mix_stage<PREC>(x, RB, RA, true, g3);
         if (!ok) break;
 

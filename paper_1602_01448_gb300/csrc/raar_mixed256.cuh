@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed256_kernel(const FrameArgs a
             float g0 = 1.f, g1 = 1.f, g2 = 1.f, g3 = 1.f;
             if constexpr (G::F16) g0 = mix_pow2_scale(mix_block_max<PREC>(x, mx));
             if (!(ok = mix_stage<PREC>(x, RA, RB, false, g0))) break;
-            if constexpr (G::F16) g1 = mix_pow2_scale(mix_region_max<PREC>(x, RB));
+            if constexpr (G::F16) g1 = kMixStage2Scale;
             if (!(ok = mix_stage<PREC>(x, RB, RA, false, g1))) break;
 
             // Fourier step on P: lane kappa2, column kappa1 -> frequency
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(512, 1) raar_mixed256_kernel(const FrameArgs a
             }
 
             if (!(ok = mix_stage<PREC>(x, RA, RB, true, g2))) break;
-            if constexpr (G::F16) g3 = mix_pow2_scale(mix_region_max<PREC>(x, RB));
+            if constexpr (G::F16) g3 = kMixStage2Scale;
             if (!(ok = mix_stage<PREC>(x, RB, RA, true, g3))) break;
             const float inv = 1.f / (g2 * g3);
 
