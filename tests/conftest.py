@@ -25,3 +25,12 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter):
+    util = sys.modules.get("tests.gpu_util")
+    notes = getattr(util, "NOTES", None)
+    if notes:
+        terminalreporter.section("measured by the GPU tests")
+        for text in notes:
+            terminalreporter.write_line(text)

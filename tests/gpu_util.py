@@ -1,6 +1,18 @@
-"""Helpers shared by the GPU parity tests (tensor transfer and error norms)."""
+"""Helpers shared by the GPU parity tests (tensor transfer, error norms and
+the measured figures reported at the end of the run)."""
 import numpy as np
 import torch
+
+# Figures the tests measured (errors, ratios against the oracle), listed by
+# the terminal summary of the run (tests/conftest.py), so that they appear in
+# the output of a quiet run.
+NOTES = []
+
+
+def note(*parts):
+    text = " ".join(str(p) for p in parts)
+    NOTES.append(text)
+    print(text)
 
 
 def dev(x, dtype=None):

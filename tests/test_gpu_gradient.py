@@ -15,7 +15,7 @@ import torch
 
 import oracle as O
 import synth
-from tests.gpu_util import dev
+from tests.gpu_util import dev, note
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +49,7 @@ def test_adam_on_amplitude_loss_and_raar_reach_the_noise_floor():
         opt.step()
         losses.append(loss.item())
     e_adam = plan.solution_error(psi.detach(), tobj, tw)[0].item()
-    print(f"eps_0 after {STEPS} steps: RAAR {e_raar:.4f}, Adam(lr={ADAM_LR}) {e_adam:.4f}; "
+    note(f"eps_0 after {STEPS} steps: RAAR {e_raar:.4f}, Adam(lr={ADAM_LR}) {e_adam:.4f}; "
           f"loss {losses[0]:.4g} -> {losses[-1]:.4g}")
     assert losses[-1] < losses[0] / 30
     assert e_raar < 0.075 and e_adam < 0.08

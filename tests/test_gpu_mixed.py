@@ -21,7 +21,7 @@ import torch
 
 import oracle as O
 import synth
-from tests.gpu_util import dev, host, rel_l2
+from tests.gpu_util import dev, host, rel_l2, note
 
 pytestmark = pytest.mark.gpu
 
@@ -63,7 +63,7 @@ def test_mixed_fourier_projection(prec):
     ref = O.data_project(z, a32)
     got = host(out)
     err = rel_l2(got, ref)
-    print(f"{prec}: P_a relative L2 error {err:.3e}")
+    note(f"{prec}: P_a relative L2 error {err:.3e}")
     assert err < TOL[prec]
     for i in range(len(pos)):
         if np.any(ref[i] != 0):
@@ -128,7 +128,7 @@ def test_mixed_raar_steps_match_oracle(prec, probe_every):
     D = O.illumination(ref["w"], pos, shape)
     vis = D > 1e-3 * D.max()
     err = rel_l2(host(plan.psi), ref["psi"], vis)
-    print(f"{prec} probe_every={probe_every}: object error after {n_steps} steps {err:.3e}")
+    note(f"{prec} probe_every={probe_every}: object error after {n_steps} steps {err:.3e}")
     assert err < 2 * n_steps * TOL[prec]
     if probe_every:
         assert rel_l2(host(plan.probe), ref["w"]) < 2 * n_steps * TOL[prec]
@@ -212,7 +212,7 @@ def test_mixed_nrmse_trajectory_against_oracle(prec):
         if it % 10 == 0:
             e_gpu = plan.solution_error(plan.psi, tobj, tw)[0].item()
             ratios[it] = (e_gpu, e_ref[it - 1])
-    print(prec, "eps_0 (GPU, oracle) by iteration:", {k: (f"{g:.3e}", f"{r:.3e}") for k, (g, r) in ratios.items()})
+    note(prec, "eps_0 (GPU, oracle) by iteration:", {k: (f"{g:.3e}", f"{r:.3e}") for k, (g, r) in ratios.items()})
     for it, (g, r) in ratios.items():
         if r > floor:
             assert g <= 1.02 * r, (it, g, r)
@@ -321,7 +321,7 @@ def test_mixed256_fourier_projection(prec):
     ref = O.data_project(z, a.astype(np.float32).astype(np.float64))
     got = host(out)
     err = rel_l2(got, ref)
-    print(f"{prec}: 256^2 P_a relative L2 error {err:.3e}")
+    note(f"{prec}: 256^2 P_a relative L2 error {err:.3e}")
     assert err < TOL[prec]
     for i in range(K):
         if np.any(ref[i] != 0):
@@ -364,7 +364,7 @@ def test_mixed256_raar_steps_match_oracle(prec, probe_every):
     D = O.illumination(ref["w"], pos, shape)
     vis = D > 1e-3 * D.max()
     err = rel_l2(host(plan.psi), ref["psi"], vis)
-    print(f"{prec} 256^2 probe_every={probe_every}: object error after {n_steps} steps {err:.3e}")
+    note(f"{prec} 256^2 probe_every={probe_every}: object error after {n_steps} steps {err:.3e}")
     assert err < 2 * n_steps * TOL[prec]
     if probe_every:
         assert rel_l2(host(plan.probe), ref["w"]) < 2 * n_steps * TOL[prec]

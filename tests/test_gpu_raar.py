@@ -6,7 +6,7 @@ import torch
 
 import oracle as O
 import synth
-from tests.gpu_util import dev, host, rel_l2
+from tests.gpu_util import dev, host, rel_l2, note
 
 pytestmark = pytest.mark.gpu
 
@@ -142,7 +142,7 @@ def test_raar_beta_range_matches_oracle(beta):
     D = O.illumination(w, pos, shape)
     vis = D > 1e-3 * D.max()
     err = rel_l2(host(plan.psi), ref["psi"], vis)
-    print(f"beta {beta}: object rel err {err:.2e} after {n_steps} steps (bound {_beta_tolerance(beta, n_steps):.1e})")
+    note(f"beta {beta}: object rel err {err:.2e} after {n_steps} steps (bound {_beta_tolerance(beta, n_steps):.1e})")
     assert err < _beta_tolerance(beta, n_steps)
 
 
@@ -215,7 +215,7 @@ def test_small_raster_nrmse_within_2_percent_of_oracle():
             ratios[it] = e_gpu / e_ref[it - 1]
     e_host = O.eps_0_object(host(plan.psi), s.obj, s.probe, s.pos, s.shape)
     assert abs(e_gpu - e_host) < 1e-3 * e_host + 1e-9
-    print("eps_0 ratio GPU/oracle by iteration:", {k: round(v, 4) for k, v in ratios.items()})
+    note("eps_0 ratio GPU/oracle by iteration:", {k: round(v, 4) for k, v in ratios.items()})
     for it, r in ratios.items():
         assert r <= 1.02, (it, r, ratios)
 
@@ -328,6 +328,6 @@ def test_large_frames_nrmse_trajectory_against_oracle():
         plan.raar_step(ta, metrics=False)
         if it % 4 == 0:
             out[it] = (plan.solution_error(plan.psi, tobj, tw)[0].item(), e_ref[it - 1])
-    print("256^2 eps_0 (GPU, oracle):", {k: (f"{g:.4e}", f"{r:.4e}") for k, (g, r) in out.items()})
+    note("256^2 eps_0 (GPU, oracle):", {k: (f"{g:.4e}", f"{r:.4e}") for k, (g, r) in out.items()})
     for it, (g, r) in out.items():
         assert abs(g / r - 1) <= 0.02, (it, g, r)
