@@ -303,6 +303,28 @@ __device__ __forceinline__ bool mix_stage(MixCtx& x, uint32_t src, uint32_t dst,
     }
 }
 
+// FP16S contraction stage in place: region r = F(or F*) . (g * region r)^T.
+// Both K-chunks of the source are converted into the B buffer before any MMA
+// writes the region.  False if the MMA completion wait gave up.
+template <int PREC>
+__device__ __forceinline__ bool mix_stage_ip(MixCtx& x, uint32_t r, bool inverse, float g) {
+    using G = MixGeo<PREC>;
+    static_assert(G::NBUF == 2, "in-place stages need both K-chunks in shared memory");
+#pragma unroll
+    for (int j = 0; j < 2; ++j) mix_convert<PREC>(x, r, j, x.sB + j * G::B_SLOT, g);
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (x.leader) {
+        tc_fence_after();
+#pragma unroll
+        for (int j = 0; j < 2; ++j) mix_issue<PREC>(x.sA, x.sB + j * G::B_SLOT, x.tbase + r, j, inverse);
+        mma_commit(x.bar);
+    }
+    x.mma_pending = true;
+    return mix_wait<PREC>(x);
+}
+
 template <int PREC, int MODE, int FLAGS, int WRAP>
 __global__ void __launch_bounds__(512, 1) raar_mixed_kernel(const FrameArgs ap) {
     using G = MixGeo<PREC>;

@@ -19,13 +19,19 @@
 //   c[nu1 + 128 p][nu2 + 128 q]
 //     = 1/2 sum_ab (-1)^(a p + b q) omega^-(a nu1 + b nu2) F128^-1(U_ab)[nu1][nu2].
 // Both ends of the split need all four sub-problems at one (nu1, nu2): the
-// load phase forms all four y_ab from the four quadrants of z and parks
-// three of them in the block's slab (FP32, 128 KB each, thread-private
-// entries, so no synchronisation is needed between writer and reader); the
-// inverse results of the first three sub-problems go to the slab the same
-// way and the last stays in tensor memory for the final combination, which
-// also runs the epilogue (state store, overlap scatter relative to the
-// object, as the FP32 frame pass).
+// load phase forms all four y_ab from the four quadrants of z; the final
+// combination of the four inverse results also runs the epilogue (state
+// store, overlap scatter relative to the object, as the FP32 frame pass).
+// Sub-problems wait in the block's slab (FP32, 128 KB per slot,
+// thread-private entries, so no synchronisation is needed between writer and
+// reader):
+//  - BF16X3 (out-of-place stages through both TMEM regions): y_00 in P,
+//    y_01 / y_10 / y_11 in slots 1-3; the inverse results of the first three
+//    sub-problems go back to slots 0-2, the last stays in P.
+//  - FP16S (in-place stages, one region per sub-problem): y_00 in P, y_01 in
+//    Q, y_10 / y_11 in slots 0 / 1; before sub-problem 1b the finished 0b
+//    swaps places with it (region <-> slot b), so two slots suffice and the
+//    final combination reads 00 and 01 from the slab, 10 and 11 from P and Q.
 //
 // Thread layout and TMEM regions as in raar_mixed.cuh: thread t owns lane
 // r = nu2 (frame column within a quadrant) and 32 row indices nu1; regions P
@@ -123,14 +129,15 @@ __global__ void __launch_bounds__(512, 1) raar_mixed256_kernel(const FrameArgs a
         const int px = RAAR ? a.pos[2 * i + 1] : 0;
 
         // ---------------------------------------------- load: the four y_ab
-        // y_00 into P, y_01 / y_10 / y_11 into slab slots 1-3
-        float mx = 0.f;
+        // y_00 into P; FP16S: y_01 into Q, y_10 / y_11 into slab slots 0 / 1;
+        // BF16X3: y_01 / y_10 / y_11 into slab slots 1-3
+        float mx = 0.f, mx1 = 0.f;
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
 #pragma unroll 1
             for (int hh = 0; hh < CW / 8; ++hh) {
                 const int n0 = mix_col<PREC>(j, x.h) + 8 * hh;
-                float zr[8], zi[8];
+                float zr[8], zi[8], zr1[8], zi1[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int nu1 = n0 + k;
@@ -183,102 +190,283 @@ __global__ void __launch_bounds__(512, 1) raar_mixed256_kernel(const FrameArgs a
                     zr[k] = y00.x;
                     zi[k] = y00.y;
                     mx = fmaxf(mx, fmaxf(fabsf(y00.x), fabsf(y00.y)));
-                    st_hint(slab_at(1, nu1), y01, pol_keep);
-                    st_hint(slab_at(2, nu1), y10, pol_keep);
-                    st_hint(slab_at(3, nu1), y11, pol_keep);
+                    if constexpr (G::F16) {
+                        zr1[k] = y01.x;
+                        zi1[k] = y01.y;
+                        mx1 = fmaxf(mx1, fmaxf(fabsf(y01.x), fabsf(y01.y)));
+                        st_hint(slab_at(0, nu1), y10, pol_keep);
+                        st_hint(slab_at(1, nu1), y11, pol_keep);
+                    } else {
+                        st_hint(slab_at(1, nu1), y01, pol_keep);
+                        st_hint(slab_at(2, nu1), y10, pol_keep);
+                        st_hint(slab_at(3, nu1), y11, pol_keep);
+                    }
                 }
                 tmem_st8x2(x.tl + RA + n0, x.tl + RA + 128 + n0, zr, zi);
+                if constexpr (G::F16) tmem_st8x2(x.tl + RB + n0, x.tl + RB + 128 + n0, zr1, zi1);
             }
         }
         tmem_wait_st();
 
         // ---------------------------------------------- four sub-problems
         const float rho = 1.f - b;
-#pragma unroll 1
-        for (int sub = 0; sub < 4 && ok; ++sub) {
-            const int sa = sub >> 1, sb = sub & 1;
-            if (sub > 0) {   // y_ab from the slab into P
-                mx = 0.f;
+        // combination of the four inverse sub-problems at row nu1 (y'_ab, the
+        // twiddles applied here) and the epilogue of its four frame samples
+        auto finish_row = [&](int nu1, float2 y00, float2 y01, float2 y10, float2 y11) {
+            const float2 u00 = y00;
+            const float2 u01 = cmulc(s_om[nu2], y01);
+            const float2 u10 = cmulc(s_om[nu1], y10);
+            const float2 u11 = cmulc(s_om[nu1 + nu2], y11);
+            const float2 e0 = cadd(u00, u10), e1 = csub(u00, u10);   // row quadrant p = 0, 1
+            const float2 f0 = cadd(u01, u11), f1 = csub(u01, u11);
+            float2 cn[4];
+            cn[0] = cscale(cadd(e0, f0), 0.5f);   // (p, q) = (0, 0)
+            cn[1] = cscale(csub(e0, f0), 0.5f);   // (0, 1)
+            cn[2] = cscale(cadd(e1, f1), 0.5f);   // (1, 0)
+            cn[3] = cscale(csub(e1, f1), 0.5f);   // (1, 1)
+            if constexpr (RAAR) {
+                float2 wp[4], pv[4];
 #pragma unroll
+                for (int pq = 0; pq < 4; ++pq) {
+                    const int y = nu1 + H * (pq >> 1), xx = nu2 + H * (pq & 1);
+                    wp[pq] = ld_hint(a.w_proj + y * M + xx, pol_keep);
+                    pv[pq] = ld_hint(a.psi + obj_index(py, px, y, xx, a.ny, a.nx, WRAP), pol_keep);
+                }
+#pragma unroll
+                for (int pq = 0; pq < 4; ++pq) {
+                    const int y = nu1 + H * (pq >> 1), xx = nu2 + H * (pq & 1);
+                    const int o = obj_index(py, px, y, xx, a.ny, a.nx, WRAP);
+                    st_hint(a.c + fo + y * M + xx, cn[pq], pol_stream);
+                    // C' += conj(w) (c_new - (1-b) w psi), relative to the object
+                    if (!a.no_scatter)
+                        red_hint(a.accA + o, cmulc(wp[pq], csub(cn[pq], cscale(cmul(wp[pq], pv[pq]), rho))),
+                                 pol_keep);
+                    if (a.write_e) red_hint(a.ebuf + fo + y * M + xx, cn[pq], pol_stream);
+                }
+            } else {
+#pragma unroll
+                for (int pq = 0; pq < 4; ++pq)
+                    st_hint(a.zout + fo + (nu1 + H * (pq >> 1)) * M + nu2 + H * (pq & 1), cn[pq],
+                            pol_stream);
+            }
+        };
+        if constexpr (G::F16) {
+            // Each sub-problem is transformed in place in one TMEM region (a
+            // stage converts both K-chunks of its source into shared memory
+            // before its MMAs overwrite it): sub-problems 00 and 10 in P, 01
+            // and 11 in Q.  Before sub-problems 10 and 11 a finished
+            // sub-problem leaves its region for the slab slot that held the
+            // pending one, entry by entry (thread-private), scaled on the way.
+            float invs[4];
+#pragma unroll 1
+            for (int sub = 0; sub < 4 && ok; ++sub) {
+                const int sa = sub >> 1, sb = sub & 1;
+                const uint32_t R = sb ? RB : RA;
+                float msub = sb ? mx1 : mx;
+                if (sub >= 2) {   // y'_{0 sb} out to slab slot sb, y_{1 sb} in
+                    msub = 0.f;
+                    const float so = invs[sub - 2];
+#pragma unroll 1
+                    for (int j = 0; j < 2; ++j) {
+#pragma unroll 1
+                        for (int hh = 0; hh < CW / 8; ++hh) {
+                            const int n0 = mix_col<PREC>(j, x.h) + 8 * hh;
+                            float ore[8], oim[8], zr[8], zi[8];
+                            tmem_ld_cols2<8>(x.tl + R + n0, x.tl + R + 128 + n0, ore, oim);
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const float2 v = ld_hint(slab_at(sb, n0 + k), pol_keep);
+                                zr[k] = v.x;
+                                zi[k] = v.y;
+                                msub = fmaxf(msub, fmaxf(fabsf(v.x), fabsf(v.y)));
+                            }
+#pragma unroll
+                            for (int k = 0; k < 8; ++k)
+                                st_hint(slab_at(sb, n0 + k), make_float2(ore[k] * so, oim[k] * so), pol_keep);
+                            tmem_st8x2(x.tl + R + n0, x.tl + R + 128 + n0, zr, zi);
+                        }
+                    }
+                    tmem_wait_st();
+                }
+                const float g0 = mix_pow2_scale(mix_block_max<PREC>(x, msub));
+                const float g1 = kMixStage2Scale;
+                if (!(ok = mix_stage_ip<PREC>(x, R, false, g0))) break;
+                if (!(ok = mix_stage_ip<PREC>(x, R, false, g1))) break;
+                float g2;
+                {   // Fourier step on R: lane kappa2, column kappa1 -> frequency
+                    // (2 kappa1 + a, 2 kappa2 + b); Z = X / 2 on the unitary scale
+                    const float inv = 0.5f / (g0 * g1);
+                    float um = 0.f;
+                    const int kx = 2 * nu2 + sb;
+#pragma unroll 1
+                    for (int j = 0; j < 2; ++j) {
+#pragma unroll
+                        for (int s = 0; s < CW / 16; ++s) {
+                            const int k0 = mix_col<PREC>(j, x.h) + 16 * s;
+                            float re[16], im[16];
+                            tmem_ld16x2(x.tl + R + k0, x.tl + R + 128 + k0, re, im);
+                            float av[16];
+#pragma unroll
+                            for (int t = 0; t < 16; ++t)
+                                av[t] = __ldcs(a.amp + fo + (size_t)(2 * (k0 + t) + sa) * M + kx);
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) {
+                                const float X = re[t] * inv, Y = im[t] * inv;
+                                const float m2 = fmaf(X, X, Y * Y);
+                                const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
+                                const float d = av[t] - m2 * rs;
+                                acc[0] += d * d;
+                                acc[1] += av[t] * av[t];
+                                bad |= (int)bad_amplitude(av[t]);
+                                if (m2 > 0.f) {
+                                    const float f = fmaf(cp * av[t], rs, b);
+                                    re[t] = X * f;
+                                    im[t] = Y * f;
+                                } else {
+                                    re[t] = cp * av[t];
+                                    im[t] = 0.f;
+                                }
+                                um = fmaxf(um, fmaxf(fabsf(re[t]), fabsf(im[t])));
+                            }
+                            float r8[8], i8[8];
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) { r8[t] = re[t]; i8[t] = im[t]; }
+                            tmem_st8x2(x.tl + R + k0, x.tl + R + 128 + k0, r8, i8);
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) { r8[t] = re[8 + t]; i8[t] = im[8 + t]; }
+                            tmem_st8x2(x.tl + R + k0 + 8, x.tl + R + 128 + k0 + 8, r8, i8);
+                        }
+                    }
+                    tmem_wait_st();
+                    g2 = mix_pow2_scale(mix_block_max<PREC>(x, um));
+                }
+                const float g3 = kMixStage2Scale;
+                if (!(ok = mix_stage_ip<PREC>(x, R, true, g2))) break;
+                if (!(ok = mix_stage_ip<PREC>(x, R, true, g3))) break;
+                invs[sub] = 1.f / (g2 * g3);
+            }
+            if (ok) {   // ---------------------------------- combination + epilogue
+                if (x.leader) prefetch_frame(i + gridDim.x);
+                const float i2 = invs[2], i3 = invs[3];
+#pragma unroll 1
                 for (int j = 0; j < 2; ++j) {
 #pragma unroll 1
                     for (int hh = 0; hh < CW / 8; ++hh) {
                         const int n0 = mix_col<PREC>(j, x.h) + 8 * hh;
-                        float zr[8], zi[8];
+                        float are[8], aim[8], bre[8], bim[8];
+                        tmem_ld_cols2<8>(x.tl + RA + n0, x.tl + RA + 128 + n0, are, aim);
+                        tmem_ld_cols2<8>(x.tl + RB + n0, x.tl + RB + 128 + n0, bre, bim);
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const float2 v = ld_hint(slab_at(sub, n0 + k), pol_keep);
-                            zr[k] = v.x;
-                            zi[k] = v.y;
-                            mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
-                        }
-                        tmem_st8x2(x.tl + RA + n0, x.tl + RA + 128 + n0, zr, zi);
+                        for (int t = 0; t < 8; ++t)
+                            finish_row(n0 + t, ld_hint(slab_at(0, n0 + t), pol_keep),
+                                       ld_hint(slab_at(1, n0 + t), pol_keep), make_float2(are[t] * i2, aim[t] * i2),
+                                       make_float2(bre[t] * i3, bim[t] * i3));
                     }
                 }
-                tmem_wait_st();
             }
-            float g0 = 1.f, g1 = 1.f, g2 = 1.f, g3 = 1.f;
-            if constexpr (G::F16) g0 = mix_pow2_scale(mix_block_max<PREC>(x, mx));
-            if (!(ok = mix_stage<PREC>(x, RA, RB, false, g0))) break;
-            if constexpr (G::F16) g1 = kMixStage2Scale;
-            if (!(ok = mix_stage<PREC>(x, RB, RA, false, g1))) break;
-
-            // Fourier step on P: lane kappa2, column kappa1 -> frequency
-            // (2 kappa1 + a, 2 kappa2 + b) of the frame; Z = X / 2 on the
-            // unitary 256^2 scale
-            {
-                const float inv = 0.5f / (g0 * g1);   // exact: powers of two
-                float um = 0.f;
-                const int kx = 2 * nu2 + sb;
+        } else {
 #pragma unroll 1
-                for (int j = 0; j < 2; ++j) {
+            for (int sub = 0; sub < 4 && ok; ++sub) {
+                const int sa = sub >> 1, sb = sub & 1;
+                if (sub > 0) {   // y_ab from the slab into P
+                    mx = 0.f;
 #pragma unroll
-                    for (int s = 0; s < CW / 16; ++s) {
-                        const int k0 = mix_col<PREC>(j, x.h) + 16 * s;
-                        float re[16], im[16];
-                        tmem_ld16x2(x.tl + RA + k0, x.tl + RA + 128 + k0, re, im);
-                        float av[16];
+                    for (int j = 0; j < 2; ++j) {
+#pragma unroll 1
+                        for (int hh = 0; hh < CW / 8; ++hh) {
+                            const int n0 = mix_col<PREC>(j, x.h) + 8 * hh;
+                            float zr[8], zi[8];
 #pragma unroll
-                        for (int t = 0; t < 16; ++t) av[t] = __ldcs(a.amp + fo + (size_t)(2 * (k0 + t) + sa) * M + kx);
-                        float ur[16], ui[16];
-#pragma unroll
-                        for (int t = 0; t < 16; ++t) {
-                            const float X = re[t] * inv, Y = im[t] * inv;
-                            const float m2 = fmaf(X, X, Y * Y);
-                            const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
-                            const float d = av[t] - m2 * rs;
-                            acc[0] += d * d;
-                            acc[1] += av[t] * av[t];
-                            bad |= (int)bad_amplitude(av[t]);
-                            if (m2 > 0.f) {
-                                const float f = fmaf(cp * av[t], rs, b);
-                                ur[t] = X * f;
-                                ui[t] = Y * f;
-                            } else {
-                                ur[t] = cp * av[t];
-                                ui[t] = 0.f;
+                            for (int k = 0; k < 8; ++k) {
+                                const float2 v = ld_hint(slab_at(sub, n0 + k), pol_keep);
+                                zr[k] = v.x;
+                                zi[k] = v.y;
+                                mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
                             }
-                            um = fmaxf(um, fmaxf(fabsf(ur[t]), fabsf(ui[t])));
+                            tmem_st8x2(x.tl + RA + n0, x.tl + RA + 128 + n0, zr, zi);
                         }
-                        float r8[8], i8[8];
-#pragma unroll
-                        for (int t = 0; t < 8; ++t) { r8[t] = ur[t]; i8[t] = ui[t]; }
-                        tmem_st8x2(x.tl + RA + k0, x.tl + RA + 128 + k0, r8, i8);
-#pragma unroll
-                        for (int t = 0; t < 8; ++t) { r8[t] = ur[8 + t]; i8[t] = ui[8 + t]; }
-                        tmem_st8x2(x.tl + RA + k0 + 8, x.tl + RA + 128 + k0 + 8, r8, i8);
                     }
+                    tmem_wait_st();
                 }
-                tmem_wait_st();
-                if constexpr (G::F16) g2 = mix_pow2_scale(mix_block_max<PREC>(x, um));
-            }
+                float g0 = 1.f, g1 = 1.f, g2 = 1.f, g3 = 1.f;
+                if constexpr (G::F16) g0 = mix_pow2_scale(mix_block_max<PREC>(x, mx));
+                if (!(ok = mix_stage<PREC>(x, RA, RB, false, g0))) break;
+                if constexpr (G::F16) g1 = kMixStage2Scale;
+                if (!(ok = mix_stage<PREC>(x, RB, RA, false, g1))) break;
 
-            if (!(ok = mix_stage<PREC>(x, RA, RB, true, g2))) break;
-            if constexpr (G::F16) g3 = kMixStage2Scale;
-            if (!(ok = mix_stage<PREC>(x, RB, RA, true, g3))) break;
-            const float inv = 1.f / (g2 * g3);
+                // Fourier step on P: lane kappa2, column kappa1 -> frequency
+                // (2 kappa1 + a, 2 kappa2 + b) of the frame; Z = X / 2 on the
+                // unitary 256^2 scale
+                {
+                    const float inv = 0.5f / (g0 * g1);   // exact: powers of two
+                    float um = 0.f;
+                    const int kx = 2 * nu2 + sb;
+#pragma unroll 1
+                    for (int j = 0; j < 2; ++j) {
+#pragma unroll
+                        for (int s = 0; s < CW / 16; ++s) {
+                            const int k0 = mix_col<PREC>(j, x.h) + 16 * s;
+                            float re[16], im[16];
+                            tmem_ld16x2(x.tl + RA + k0, x.tl + RA + 128 + k0, re, im);
+                            float av[16];
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) av[t] = __ldcs(a.amp + fo + (size_t)(2 * (k0 + t) + sa) * M + kx);
+                            float ur[16], ui[16];
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) {
+                                const float X = re[t] * inv, Y = im[t] * inv;
+                                const float m2 = fmaf(X, X, Y * Y);
+                                const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
+                                const float d = av[t] - m2 * rs;
+                                acc[0] += d * d;
+                                acc[1] += av[t] * av[t];
+                                bad |= (int)bad_amplitude(av[t]);
+                                if (m2 > 0.f) {
+                                    const float f = fmaf(cp * av[t], rs, b);
+                                    ur[t] = X * f;
+                                    ui[t] = Y * f;
+                                } else {
+                                    ur[t] = cp * av[t];
+                                    ui[t] = 0.f;
+                                }
+                                um = fmaxf(um, fmaxf(fabsf(ur[t]), fabsf(ui[t])));
+                            }
+                            float r8[8], i8[8];
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) { r8[t] = ur[t]; i8[t] = ui[t]; }
+                            tmem_st8x2(x.tl + RA + k0, x.tl + RA + 128 + k0, r8, i8);
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) { r8[t] = ur[8 + t]; i8[t] = ui[8 + t]; }
+                            tmem_st8x2(x.tl + RA + k0 + 8, x.tl + RA + 128 + k0 + 8, r8, i8);
+                        }
+                    }
+                    tmem_wait_st();
+                    if constexpr (G::F16) g2 = mix_pow2_scale(mix_block_max<PREC>(x, um));
+                }
 
-            if (sub < 3) {   // F128^-1(U_ab) into slab slot sub (its y_ab is consumed)
+                if (!(ok = mix_stage<PREC>(x, RA, RB, true, g2))) break;
+                if constexpr (G::F16) g3 = kMixStage2Scale;
+                if (!(ok = mix_stage<PREC>(x, RB, RA, true, g3))) break;
+                const float inv = 1.f / (g2 * g3);
+
+                if (sub < 3) {   // F128^-1(U_ab) into slab slot sub (its y_ab is consumed)
+#pragma unroll 1
+                    for (int j = 0; j < 2; ++j) {
+#pragma unroll
+                        for (int s = 0; s < CW / 16; ++s) {
+                            const int n0 = mix_col<PREC>(j, x.h) + 16 * s;
+                            float re[16], im[16];
+                            tmem_ld16x2(x.tl + RA + n0, x.tl + RA + 128 + n0, re, im);
+#pragma unroll
+                            for (int t = 0; t < 16; ++t)
+                                st_hint(slab_at(sub, n0 + t), make_float2(re[t] * inv, im[t] * inv), pol_keep);
+                        }
+                    }
+                    continue;
+                }
+
+                // ------------------------------------------ combination + epilogue
+                if (x.leader) prefetch_frame(i + gridDim.x);
 #pragma unroll 1
                 for (int j = 0; j < 2; ++j) {
 #pragma unroll
@@ -287,60 +475,10 @@ __global__ void __launch_bounds__(512, 1) raar_mixed256_kernel(const FrameArgs a
                         float re[16], im[16];
                         tmem_ld16x2(x.tl + RA + n0, x.tl + RA + 128 + n0, re, im);
 #pragma unroll
-                        for (int t = 0; t < 16; ++t)
-                            st_hint(slab_at(sub, n0 + t), make_float2(re[t] * inv, im[t] * inv), pol_keep);
-                    }
-                }
-                continue;
-            }
-
-            // ------------------------------------------ combination + epilogue
-            if (x.leader) prefetch_frame(i + gridDim.x);
-#pragma unroll 1
-            for (int j = 0; j < 2; ++j) {
-#pragma unroll
-                for (int s = 0; s < CW / 16; ++s) {
-                    const int n0 = mix_col<PREC>(j, x.h) + 16 * s;
-                    float re[16], im[16];
-                    tmem_ld16x2(x.tl + RA + n0, x.tl + RA + 128 + n0, re, im);
-#pragma unroll
-                    for (int t = 0; t < 16; ++t) {
-                        const int nu1 = n0 + t;
-                        const float2 u00 = ld_hint(slab_at(0, nu1), pol_keep);
-                        const float2 u01 = cmulc(s_om[nu2], ld_hint(slab_at(1, nu1), pol_keep));
-                        const float2 u10 = cmulc(s_om[nu1], ld_hint(slab_at(2, nu1), pol_keep));
-                        const float2 u11 = cmulc(s_om[nu1 + nu2], make_float2(re[t] * inv, im[t] * inv));
-                        const float2 e0 = cadd(u00, u10), e1 = csub(u00, u10);   // row quadrant p = 0, 1
-                        const float2 f0 = cadd(u01, u11), f1 = csub(u01, u11);
-                        float2 cn[4];
-                        cn[0] = cscale(cadd(e0, f0), 0.5f);   // (p, q) = (0, 0)
-                        cn[1] = cscale(csub(e0, f0), 0.5f);   // (0, 1)
-                        cn[2] = cscale(cadd(e1, f1), 0.5f);   // (1, 0)
-                        cn[3] = cscale(csub(e1, f1), 0.5f);   // (1, 1)
-                        if constexpr (RAAR) {
-                            float2 wp[4], pv[4];
-#pragma unroll
-                            for (int pq = 0; pq < 4; ++pq) {
-                                const int y = nu1 + H * (pq >> 1), xx = nu2 + H * (pq & 1);
-                                wp[pq] = ld_hint(a.w_proj + y * M + xx, pol_keep);
-                                pv[pq] = ld_hint(a.psi + obj_index(py, px, y, xx, a.ny, a.nx, WRAP), pol_keep);
-                            }
-#pragma unroll
-                            for (int pq = 0; pq < 4; ++pq) {
-                                const int y = nu1 + H * (pq >> 1), xx = nu2 + H * (pq & 1);
-                                const int o = obj_index(py, px, y, xx, a.ny, a.nx, WRAP);
-                                st_hint(a.c + fo + y * M + xx, cn[pq], pol_stream);
-                                // C' += conj(w) (c_new - (1-b) w psi), relative to the object
-                                if (!a.no_scatter)
-                                    red_hint(a.accA + o, cmulc(wp[pq], csub(cn[pq], cscale(cmul(wp[pq], pv[pq]), rho))),
-                                             pol_keep);
-                                if (a.write_e) red_hint(a.ebuf + fo + y * M + xx, cn[pq], pol_stream);
-                            }
-                        } else {
-#pragma unroll
-                            for (int pq = 0; pq < 4; ++pq)
-                                st_hint(a.zout + fo + (nu1 + H * (pq >> 1)) * M + nu2 + H * (pq & 1), cn[pq],
-                                        pol_stream);
+                        for (int t = 0; t < 16; ++t) {
+                            const int nu1 = n0 + t;
+                            finish_row(nu1, ld_hint(slab_at(0, nu1), pol_keep), ld_hint(slab_at(1, nu1), pol_keep),
+                                       ld_hint(slab_at(2, nu1), pol_keep), make_float2(re[t] * inv, im[t] * inv));
                         }
                     }
                 }
