@@ -2,7 +2,8 @@
 
 * A bounded wait that runs out: the plan's wait limit set to zero polls makes
   every first wait of a frame pass (bulk copy of the frame state, tensor-core
-  MMA completion) give up at once.  The kernel then drains its own copies and
+  MMA completion, at 128^2 and in the 256^2 tensor-core passes) give up at
+  once.  The kernel then drains its own copies and
   MMAs in flight with the full limit, releases its tensor memory and returns;
   sharp_plan_status reports SHARP_ERR_TIMEOUT once, and the plan, restarted
   with the default limit, matches the FP64 oracle again (Sec. 2.2 steps).
@@ -53,7 +54,8 @@ def _expect(S, plan, code):
     plan.status()   # reported once, then cleared
 
 
-@pytest.mark.parametrize("m,prec", [(64, "fp32"), (128, "fp32"), (128, "fp16s"), (128, "bf16x3")])
+@pytest.mark.parametrize("m,prec", [(64, "fp32"), (128, "fp32"), (128, "fp16s"), (128, "bf16x3"), (256, "fp16s"),
+                                    (256, "bf16x3")])
 def test_wait_that_runs_out_reports_timeout_and_the_plan_recovers(m, prec):
     S = _lib()
     w, pos, shape, a, psi0 = _scan(m, 31 + m)
