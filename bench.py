@@ -663,7 +663,7 @@ def run_batch(args, rank, world):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
-    for _ in range(max(args.warmup, 4)):        # includes the grid autotuning steps
+    for _ in range(max(args.warmup, 8)):        # covers the autotuner's candidate steps (at most 6)
         batch.step()
     sampler = ClockSampler(local)
     sampler.start()
@@ -673,6 +673,18 @@ def run_batch(args, rank, world):
     batch.status()
     ms_total = slowest_rank_ms(ms_total, world, dev)
     ms_step = ms_total / args.steps
+
+    # the tuned launch shapes against the library's defaults (one block per
+    # SM, 8 rows per round trip, 4 for 256^2, 2 us stagger): same steps again
+    sizes = sorted({sc.m for sc in scans})
+    shapes = {str(m): list(batch.tuned_shape(m)) for m in sizes}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    for m in sizes:
+        batch.set_shape(m, sms, 4 if m == 256 else 8, 2000)
+    for _ in range(3):
+        batch.step()
+    ms_default = slowest_rank_ms(timed(batch.step, args.steps), world, dev) / args.steps
+    batch.status()
 
     # the same scans stepped one after another through sharp_raar_step
     singles = [make(sc, a)[0] for sc, a in zip(scans, amps)]
@@ -686,7 +698,6 @@ def run_batch(args, rank, world):
     ms_single = timed(one_by_one, args.steps) / args.steps
     if rank != 0:
         return
-    grids = {m: batch.tuned_grid(m) for m in (64, 128, 256)}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         sc = scans[0]
@@ -707,13 +718,16 @@ def run_batch(args, rank, world):
         "config": {"workload": f"batch-{len(scans)}scans-{total}frames", "scans": len(scans), "frames": total,
                    "frames_by_size": {str(m): sum(sc.K for sc in scans if sc.m == m) for m in (64, 128, 256)},
                    "beta": 0.75, "probe_every": 0, "residual_every": RESIDUAL_EVERY,
-                   "parallelism": f"replicas{world}", "tuned_grid": grids,
+                   "parallelism": f"replicas{world}", "tuned_shape": shapes,
                    "l2": f"inputs larger than L2 ({alg_bytes * 0.6 / 1e9:.1f} GB of state + amplitudes read per step)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "whole step (all launches of sharp_batch_step)",
                      "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes, "kernel_ms": ms_step},
         "one_by_one": {"ms_per_step": ms_single, "value": total / (ms_single / 1000.0),
                        "speedup_of_batch": ms_single / ms_step},
+        "autotuner": {"shape": "[grid, rows per round trip, stagger ns] per frame size",
+                      "default_ms_per_step": ms_default, "tuned_ms_per_step": ms_step,
+                      "gain": ms_default / ms_step},
         "cpu_baseline": cpu,
         "e2e": None,
         # per step: one frame pass per frame size, then per scan the image
